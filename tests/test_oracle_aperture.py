@@ -1,0 +1,284 @@
+"""Pins of the oracle's aperture sums against closed forms, invariants and an
+independent evaluation of the paper's printed spherical formulas.
+
+  * filter: Q from U (Sect. 2), compensation of U, Schirmer limits;
+  * a direct O(N M) evaluation of Sect. 2.3's separation and tan(psi)
+    formulas with atan2 (not unit vectors) on tiny inputs;
+  * the isolated SIS: M_B = 0 and M_E = integral of Q gamma_t over the cap
+    (1-D quadrature), tending to 4 theta_E / (5 theta_ap) in the flat limit;
+  * invariants: 45-degree shear rotation, RA shift by 90 degrees, N-S
+    mirror, a general rigid rotation, constant shear;
+  * pixel mode equals brute force on the catalogue snapped to pixel centres;
+  * binning equals numpy's stable argsort / bincount.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+from scipy import integrate
+
+import oracle
+from paper_2609_11181_b300 import synth
+
+ARCMIN = math.pi / (180 * 60)
+
+
+# ------------------------------------------------------------------ filters
+def test_q_from_u_poly():
+    # Q(x) = (2/x^2) int_0^x x' U(x') dx' - U(x)   (Sect. 2, Q from U)
+    for x in [0.05, 0.2, 0.5, 0.77, 0.99]:
+        integral, _ = integrate.quad(lambda t: t * oracle.filter_u_poly(t)[0], 0, x,
+                                     epsabs=1e-14, epsrel=1e-13)
+        q = 2 / x ** 2 * integral - oracle.filter_u_poly(x)[0]
+        assert q == pytest.approx(oracle.filter_q(1, x)[0], rel=1e-11, abs=1e-14)
+
+
+def test_u_compensated():
+    x, wx = np.polynomial.legendre.leggauss(8)      # exact for this degree-5 integrand
+    t = 0.5 * (x + 1)
+    val = 0.5 * np.sum(wx * t * oracle.filter_u_poly(t))
+    assert abs(val) < 1e-14
+
+
+def test_schirmer_limits():
+    xc = 0.15
+    q0 = oracle.filter_q(2, 1e-12, xc)[0]
+    assert q0 == pytest.approx(1 / (1 + math.exp(6) + math.exp(-47)), rel=1e-9)
+    # away from both exponential cut-offs the filter is tanh(x/xc)/(x/xc)
+    x = 0.5
+    assert oracle.filter_q(2, x, xc)[0] == pytest.approx(math.tanh(x / xc) / (x / xc), rel=1e-8)
+    # the outer cut-off halves the filter where -47 + 50 x = 0
+    x = 0.94
+    assert oracle.filter_q(2, x, xc)[0] == pytest.approx(0.5 * math.tanh(x / xc) / (x / xc), rel=1e-6)
+
+
+# ---------------------------------------------- direct spherical formulas
+def _direct(c_ra, c_dec, ra, dec, e1, e2, w, kind, theta_ap):
+    """Sect. 2.3's printed formulas, evaluated with trig + atan2."""
+    a0, d0 = np.radians(c_ra), np.radians(c_dec)
+    ai, di = np.radians(ra), np.radians(dec)
+    out = []
+    for a, d in zip(a0, d0):
+        da = ai - a
+        cosd = np.sin(di) * np.sin(d) + np.cos(di) * np.cos(d) * np.cos(da)
+        # haversine for an accurate separation at small angles
+        hav = np.sin((di - d) / 2) ** 2 + np.cos(di) * np.cos(d) * np.sin(da / 2) ** 2
+        sep = 2 * np.arcsin(np.sqrt(hav))
+        assert np.allclose(np.cos(sep), cosd, atol=1e-12)
+        m = sep <= theta_ap
+        psi = np.arctan2(np.sin(da), np.cos(di) * np.tan(d) - np.sin(di) * np.cos(da))
+        q = oracle.filter_q(kind, sep[m] / theta_ap) / theta_ap ** 2
+        gp = e1[m] * np.cos(2 * psi[m]) + e2[m] * np.sin(2 * psi[m])
+        gx = -e1[m] * np.sin(2 * psi[m]) + e2[m] * np.cos(2 * psi[m])
+        out.append((np.sum(w[m] * gp * q), np.sum(w[m] * gx * q),
+                    np.sum(w[m] ** 2 * (e1[m] ** 2 + e2[m] ** 2) * q * q), np.sum(w[m]), m.sum()))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_direct_formulas_tiny(kind):
+    rng = np.random.default_rng(kind)
+    n, n0 = 600, 40
+    ra = rng.uniform(20, 26, n)
+    dec = rng.uniform(-33, -27, n)
+    e1, e2 = rng.normal(0, 0.3, n), rng.normal(0, 0.3, n)
+    w = rng.uniform(0.5, 1.5, n)
+    c_ra, c_dec = rng.uniform(21, 25, n0), rng.uniform(-32, -28, n0)
+    th = 1.5 * math.pi / 180
+    ref = _direct(c_ra, c_dec, ra, dec, e1, e2, w, kind, th)
+    cv = oracle.radec2vec(c_ra, c_dec)
+    got = oracle.aperture_galaxies(cv, ra, dec, e1, e2, w, kind, th)
+    np.testing.assert_array_equal(got["N"], ref[:, 4].astype(np.int64))
+    for k, col in (("SE", 0), ("SB", 1), ("SV", 2), ("SW", 3)):
+        np.testing.assert_allclose(got[k], ref[:, col], rtol=1e-10, atol=1e-10 * np.abs(ref[:, col]).max())
+
+
+# --------------------------------------------------------------- SIS pin
+def _polar_grid(ra0, dec0, theta_max, n_t=64, n_p=160):
+    """Gauss-Legendre nodes in theta x uniform phi around (ra0, dec0); weights = dOmega."""
+    x, wx = np.polynomial.legendre.leggauss(n_t)
+    th = 0.5 * theta_max * (x + 1)
+    wt = 0.5 * theta_max * wx * np.sin(th)
+    ph = (np.arange(n_p) + 0.5) * 2 * np.pi / n_p
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    W = np.repeat(wt[:, None], n_p, axis=1) * (2 * np.pi / n_p)
+    v = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+    # rotate +z onto (ra0, dec0)
+    t = math.pi / 2 - math.radians(dec0)
+    Ry = np.array([[math.cos(t), 0, math.sin(t)], [0, 1, 0], [-math.sin(t), 0, math.cos(t)]])
+    a = math.radians(ra0)
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    v = v @ (Rz @ Ry).T
+    ra = np.degrees(np.arctan2(v[:, 1], v[:, 0])) % 360
+    dec = np.degrees(np.arcsin(np.clip(v[:, 2], -1, 1)))
+    return ra, dec, W.ravel()
+
+
+@pytest.mark.parametrize("kind,theta_arcmin,dec0", [(1, 60, 24.0), (1, 10, -61.0), (2, 10, 5.0), (1, 600, 40.0)])
+def test_sis_closed_form(kind, theta_arcmin, dec0):
+    th = theta_arcmin * ARCMIN
+    te = 0.7 * ARCMIN
+    ra0 = 37.0
+    ra, dec, w = _polar_grid(ra0, dec0, th * (1 - 1e-9), n_t=400 if kind == 2 else 64)
+    halos = synth.Halos(torch.tensor([ra0], dtype=torch.float64), torch.tensor([dec0], dtype=torch.float64),
+                        torch.tensor([te], dtype=torch.float64))
+    g1, g2 = synth.sis_shear(torch.from_numpy(ra), torch.from_numpy(dec), halos, r_trunc=2 * th)
+    e1, e2 = g1.numpy(), g2.numpy()
+    c = oracle.radec2vec([ra0], [dec0])
+    r = oracle.map_galaxies(c, ra, dec, e1, e2, w, kind, th)
+
+    def integrand(t):
+        return 2 * math.pi * math.sin(t) * oracle.filter_q(kind, t / th)[0] / th ** 2 * te / (2 * t)
+
+    exact, _ = integrate.quad(integrand, 0, th, epsabs=1e-15, epsrel=1e-12, limit=200)
+    assert r["SW"][0] == pytest.approx(2 * math.pi * (1 - math.cos(th * (1 - 1e-9))), rel=1e-12)
+    assert r["ME"][0] == pytest.approx(exact, rel=1e-8)
+    assert abs(r["MB"][0]) < 1e-11 * abs(exact)
+    if kind == 1 and theta_arcmin <= 60:
+        flat = 4 * te / (5 * th)          # Schneider (1996) flat-sky closed form
+        assert r["ME"][0] == pytest.approx(flat, rel=2 * th ** 2)
+
+
+# ---------------------------------------------------------- invariants
+def _catalog(seed, n=4000, ra0=30.0, dec0=10.0, radius_deg=3.0, nhalo=6):
+    g = synth.make_gen(seed)
+    rad = math.radians(radius_deg)
+    halos = synth.halos_uniform(nhalo, ra0, dec0, rad, g, 0.2 * ARCMIN, 1.0 * ARCMIN)
+    cat = synth.galaxy_catalog(n, ra0, dec0, rad, halos, g, r_trunc=math.radians(2.0), w_range=(0.5, 1.5))
+    return (cat.ra_deg.numpy(), cat.dec_deg.numpy(), cat.e1.double().numpy(),
+            cat.e2.double().numpy(), cat.w.double().numpy())
+
+
+def _targets(nside, ra0, dec0, radius_deg):
+    v = oracle.pix2vec(nside, np.arange(12 * nside * nside))
+    c = oracle.radec2vec([ra0], [dec0])[0]
+    return np.nonzero(v @ c >= math.cos(math.radians(radius_deg)))[0]
+
+
+def test_shear_rotation_45():
+    ra, dec, e1, e2, w = _catalog(1)
+    tg = _targets(64, 30, 10, 2.0)
+    cv = oracle.pix2vec(64, tg)
+    th = 30 * ARCMIN
+    a = oracle.map_galaxies(cv, ra, dec, e1, e2, w, 1, th)
+    b = oracle.map_galaxies(cv, ra, dec, -e2, e1, w, 1, th)
+    sc = np.abs(a["ME"]).max()
+    np.testing.assert_allclose(b["ME"], -a["MB"], atol=1e-12 * sc)
+    np.testing.assert_allclose(b["MB"], a["ME"], atol=1e-12 * sc)
+    np.testing.assert_allclose(b["VAR"], a["VAR"], rtol=1e-12)
+
+
+def test_ra_shift_90_permutes_map():
+    nside = 64
+    ra, dec, e1, e2, w = _catalog(2)
+    tg = _targets(nside, 30, 10, 2.0)
+    th = 25 * ARCMIN
+    a = oracle.map_galaxies(oracle.pix2vec(nside, tg), ra, dec, e1, e2, w, 2, th)
+    tg2 = []
+    for p in tg:
+        ring, j, nr, *_ = oracle.pix_info(nside, int(p))
+        start, *_ = oracle.ring_info(nside, ring)
+        tg2.append(start + (j + nr // 4) % nr)
+    b = oracle.map_galaxies(oracle.pix2vec(nside, np.array(tg2)), (ra + 90.0) % 360, dec, e1, e2, w, 2, th)
+    np.testing.assert_array_equal(a["N"], b["N"])
+    sc = np.abs(a["ME"]).max()
+    np.testing.assert_allclose(b["ME"], a["ME"], atol=1e-10 * sc)
+    np.testing.assert_allclose(b["MB"], a["MB"], atol=1e-10 * sc)
+
+
+def test_north_south_mirror():
+    nside = 64
+    ra, dec, e1, e2, w = _catalog(3)
+    tg = _targets(nside, 30, 10, 2.0)
+    th = 25 * ARCMIN
+    a = oracle.map_galaxies(oracle.pix2vec(nside, tg), ra, dec, e1, e2, w, 1, th)
+    tm = []
+    for p in tg:
+        ring, j, *_ = oracle.pix_info(nside, int(p))
+        start, *_ = oracle.ring_info(nside, 4 * nside - ring)
+        tm.append(start + j)
+    b = oracle.map_galaxies(oracle.pix2vec(nside, np.array(tm)), ra, -dec, e1, -e2, w, 1, th)
+    np.testing.assert_array_equal(a["N"], b["N"])
+    sc = np.abs(a["ME"]).max()
+    np.testing.assert_allclose(b["ME"], a["ME"], atol=1e-10 * sc)
+    np.testing.assert_allclose(b["MB"], -a["MB"], atol=1e-10 * sc)
+
+
+def _basis(v):
+    rho = np.hypot(v[:, 0], v[:, 1])
+    e = np.stack([-v[:, 1] / rho, v[:, 0] / rho, np.zeros(len(v))], -1)
+    nn = np.stack([-v[:, 2] * v[:, 0] / rho, -v[:, 2] * v[:, 1] / rho, rho], -1)
+    return e, nn
+
+
+def test_rigid_rotation():
+    ra, dec, e1, e2, w = _catalog(4, n=3000)
+    v = oracle.radec2vec(ra, dec)
+    rng = np.random.default_rng(9)
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    R = q
+    vr = v @ R.T
+    ea, na = _basis(v)
+    eb, nb = _basis(vr)
+    Re = ea @ R.T
+    chi = np.arctan2((nb * Re).sum(1), (eb * Re).sum(1))      # old East seen in the new basis
+    g = (e1 + 1j * e2) * np.exp(2j * chi)
+    ra2 = np.degrees(np.arctan2(vr[:, 1], vr[:, 0])) % 360
+    dec2 = np.degrees(np.arcsin(np.clip(vr[:, 2], -1, 1)))
+    cen = oracle.radec2vec(rng.uniform(28.5, 31.5, 30), rng.uniform(8.5, 11.5, 30))
+    th = 40 * ARCMIN
+    a = oracle.map_galaxies(cen, ra, dec, e1, e2, w, 1, th)
+    b = oracle.map_galaxies(cen @ R.T, ra2, dec2, g.real, g.imag, w, 1, th)
+    np.testing.assert_array_equal(a["N"], b["N"])
+    sc = np.abs(a["ME"]).max()
+    np.testing.assert_allclose(b["ME"], a["ME"], atol=1e-9 * sc)
+    np.testing.assert_allclose(b["MB"], a["MB"], atol=1e-9 * sc)
+
+
+def test_constant_shear_vanishes():
+    # on a polar grid about an equatorial centre, a shear constant in the local
+    # basis averages out over azimuth; what is left is the O(theta^2) turn of
+    # the local basis across the aperture
+    th = 20 * ARCMIN
+    ra, dec, w = _polar_grid(123.0, 0.0, th * (1 - 1e-9))
+    e1 = np.full(ra.size, 0.1)
+    e2 = np.full(ra.size, -0.05)
+    r = oracle.map_galaxies(oracle.radec2vec([123.0], [0.0]), ra, dec, e1, e2, w, 1, th)
+    assert abs(r["ME"][0]) < 0.1 * th ** 2 and abs(r["MB"][0]) < 0.1 * th ** 2
+
+
+# --------------------------------------------- pixel mode and binning
+def test_binning_against_numpy():
+    ra, dec, e1, e2, w = _catalog(5, n=20000)
+    nside = 256
+    b = oracle.bin_catalog(nside, ra, dec, e1, e2, w)
+    pix = oracle.ang2pix(nside, ra, dec)
+    np.testing.assert_array_equal(b["pix"], pix)
+    np.testing.assert_array_equal(b["perm"], np.argsort(pix, kind="stable"))
+    npix = 12 * nside * nside
+    cnt = np.bincount(pix, minlength=npix)
+    np.testing.assert_array_equal(b["n"], cnt)
+    np.testing.assert_array_equal(b["offsets"], np.concatenate([[0], np.cumsum(cnt)]))
+    np.testing.assert_allclose(b["G1"], np.bincount(pix, w * e1, npix), atol=1e-12)
+    np.testing.assert_allclose(b["S2"], np.bincount(pix, w * w * (e1 ** 2 + e2 ** 2), npix), atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_pixel_mode_equals_snapped_brute_force(kind):
+    ra, dec, e1, e2, w = _catalog(6, n=30000)
+    nb, no = 256, 64
+    b = oracle.bin_catalog(nb, ra, dec, e1, e2, w)
+    pv = oracle.pix2vec(nb, b["pix"])
+    sra = np.degrees(np.arctan2(pv[:, 1], pv[:, 0])) % 360
+    sdec = np.degrees(np.arcsin(np.clip(pv[:, 2], -1, 1)))
+    tg = _targets(no, 30, 10, 2.2)
+    cv = oracle.pix2vec(no, tg)
+    th = 35 * ARCMIN
+    a = oracle.map_pixels(cv, nb, b["G1"], b["G2"], b["W"], b["S2"], b["n"], kind, th)
+    s = oracle.map_galaxies(cv, sra, sdec, e1, e2, w, kind, th)
+    np.testing.assert_array_equal(a["N"], s["N"])
+    for k in ("SE", "SB", "SV", "SW"):
+        np.testing.assert_allclose(a[k], s[k], rtol=1e-9, atol=1e-9 * np.abs(s[k]).max())
