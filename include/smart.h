@@ -1,0 +1,189 @@
+/*
+ * smart.h -- C ABI of the B300 (sm_103a) spherical shear-based aperture-mass
+ * library (SMART, arXiv 2609.11181).
+ *
+ * The problem (Sect. 2-3 of the paper): for every output HEALPix pixel
+ * centre theta_0, sum over the galaxies (brute force, Sect. 3.1 / 3.4) or
+ * the binned shear pixels (pixel-based, Sect. 3.2) that lie within the
+ * aperture radius theta_ap; rotate each shear into tangential and cross
+ * components with the spherical position angle (Sect. 2.3, Eq. gammat),
+ * weight by the filter Q, and normalise by the mean weight density inside
+ * the aperture (the summed approach, Sect. 2.4).  Outputs per centre:
+ * M_ap^E, M_ap^B (Eq. map), the noise variance (Eq. map_noise), the weight
+ * sum and the member count.
+ *
+ * Conventions shared by every call
+ *  - Array arguments are DEVICE pointers owned by the caller unless a
+ *    parameter says "host".  The caller keeps inputs alive until
+ *    smart_sync() returns.
+ *  - Every call is asynchronous on the context's CUDA stream (the stream
+ *    given to smart_create, 0 = legacy default stream) and returns at once;
+ *    only smart_sync() blocks.
+ *  - The library owns only its internal scratch (sorted catalogue, offsets,
+ *    ring tables, binned maps it made itself) and frees it in
+ *    smart_destroy().
+ *  - No call aborts, traps or throws.  Errors come back as a smart_status;
+ *    smart_last_error() gives a one-line description.  Argument errors are
+ *    detected on the host before anything is launched.
+ *  - Sizes are int64.  nside values must be powers of two in [1, 8192].
+ *  - Angles: ra/dec in degrees (float64); theta_ap in arcmin.  The shear
+ *    components e1, e2 are given in the local (East = +RA, North = +Dec)
+ *    basis; a positive tangential component means alignment perpendicular
+ *    to the direction of the aperture centre.
+ *  - Pixel indices are RING-scheme indices (Gorski et al. 2005, Sect. 3).
+ */
+#ifndef SMART_H
+#define SMART_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMART_OK = 0,
+    SMART_E_ARG = 1,        /* invalid argument (detected on the host)       */
+    SMART_E_NOMEM = 2,      /* device allocation failed                       */
+    SMART_E_CUDA = 3,       /* a CUDA runtime call or kernel launch failed   */
+    SMART_E_STATE = 4,      /* call order violated (e.g. map before data)    */
+    SMART_E_TIMEOUT = 5,    /* smart_sync deadline passed                    */
+    SMART_E_OVERFLOW = 6,   /* a size exceeds an internal limit              */
+    SMART_E_INTERNAL = 7
+} smart_status;
+
+typedef enum {
+    SMART_FILTER_POLY = 1,      /* Schneider (1996): Q = 6/pi x^2 (1 - x^2) / theta_ap^2      */
+    SMART_FILTER_SCHIRMER = 2   /* Schirmer et al. (2007): Q = tanh(x/xc)/(x/xc) /
+                                   (1 + e^(6-150x) + e^(-47+50x)) / theta_ap^2               */
+} smart_filter_kind;
+
+typedef struct {
+    int kind;                   /* smart_filter_kind                          */
+    double xc;                  /* Schirmer core, default 0.15; ignored else  */
+} smart_filter;
+
+/* Output buffers, one entry per target pixel (device pointers; any may be
+   NULL to skip that output). */
+typedef struct {
+    double *sum_w;      /* f64 [n]: sum of weights in the aperture (Sect. 2.4)     */
+    float *map_e;       /* f32 [n]: M_ap^E, summed normalisation (Eq. map)          */
+    float *map_b;       /* f32 [n]: M_ap^B                                          */
+    float *var;         /* f32 [n]: sigma_ap^2 (Eq. map_noise with weights)          */
+    int64_t *count;     /* i64 [n]: galaxies in the aperture (brute force) or
+                                    galaxies in the member pixels (pixel mode)    */
+    int32_t *members;   /* i32 [n]: aperture members = (centre, point) pairs summed:
+                                    galaxies (brute force) or pixels, empty or
+                                    not, whose centre is inside (pixel mode)      */
+} smart_maps;
+
+typedef struct smart_ctx smart_ctx;
+
+/*
+ * Create a context for maps on the RING grid at nside_out with aperture
+ * radius theta_ap_arcmin (0 < theta_ap <= 60 deg) and the given filter.
+ * nside_bin is the grid that galaxies are sorted / binned on (Sect. 3.2,
+ * 3.4).  cuda_stream is a cudaStream_t (may be NULL).  On success *out
+ * holds the new context; on failure *out is NULL.
+ */
+smart_status smart_create(int nside_out, const smart_filter *filter,
+                          double theta_ap_arcmin, int nside_bin,
+                          void *cuda_stream, smart_ctx **out);
+
+/* Release every device buffer the context owns.  NULL is a no-op. */
+void smart_destroy(smart_ctx *ctx);
+
+/* Block until the context's stream is idle, polling with the given deadline
+   in seconds (<= 0: wait forever).  Returns SMART_E_TIMEOUT if the deadline
+   passes (the work keeps running), SMART_E_CUDA if an asynchronous error
+   surfaced. */
+smart_status smart_sync(smart_ctx *ctx, double timeout_s);
+
+/* One-line description of the last error on this context ("" if none). */
+const char *smart_last_error(const smart_ctx *ctx);
+
+/*
+ * Target (output) pixels: n RING indices at nside_out, int64, device
+ * pointer.  They must be sorted ascending and unique.  The array is copied;
+ * the caller may free it after smart_sync.
+ */
+smart_status smart_set_targets(smart_ctx *ctx, const int64_t *ring_pix, int64_t n);
+
+/*
+ * Sect. 3.4 steps 1-3 and Sect. 3.2 step 2: assign each galaxy its RING
+ * pixel at nside_bin (bit-exact with the FP64 definition), stable-sort the
+ * catalogue by pixel with a GPU LSD radix sort, build the offset table
+ * (first galaxy of each pixel) and the per-pixel sums
+ *   G1 = sum w e1, G2 = sum w e2, W = sum w, S2 = sum w^2 (e1^2 + e2^2),
+ *   n = count
+ * in float32, accumulated in sorted order.  ra/dec: f64 degrees; e1, e2,
+ * w: f32; all device pointers of n entries.  w may be NULL (all weights 1).
+ * Replaces any binned map given earlier with smart_set_binned.
+ */
+smart_status smart_bin_galaxies(smart_ctx *ctx, const double *ra_deg,
+                                const double *dec_deg, const float *e1,
+                                const float *e2, const float *w, int64_t n);
+
+/*
+ * Give per-pixel sums directly (full-sky RING arrays at nside_bin, 12
+ * nside_bin^2 entries each, device pointers, caller-owned and not copied:
+ * keep them alive until the map calls have synced).  Same meaning as the
+ * sums of smart_bin_galaxies.  Pixel-based maps only.
+ */
+smart_status smart_set_binned(smart_ctx *ctx, const float *G1, const float *G2,
+                              const float *W, const float *S2, const int32_t *n_p);
+
+/*
+ * Brute-force map at galaxy positions (Sect. 3.1 steps 1-5; neighbours
+ * found through the sorted catalogue of Sect. 3.4).  Requires
+ * smart_bin_galaxies and smart_set_targets.  Membership is s^2 <= T with
+ * s the chord between unit vectors and T = 4 sin^2(theta_ap/2), decided
+ * exactly as in float64.
+ */
+smart_status smart_map_bruteforce(smart_ctx *ctx, const smart_maps *out);
+
+/*
+ * Pixel-based map (Sect. 3.2 steps 3-5): filter and rotation evaluated at
+ * the centres of the binned pixels whose centres are inside the aperture.
+ * Requires binned data (smart_bin_galaxies or smart_set_binned) and
+ * smart_set_targets.
+ */
+smart_status smart_map_pixel(smart_ctx *ctx, const smart_maps *out);
+
+/* ---- geometry utilities (Sect. 3, HEALPix RING; stateless) ---------- */
+
+/* pix[k] = RING pixel at nside of (ra_deg[k], dec_deg[k]); bit-exact with
+   the float64 definition.  Device pointers; stream may be NULL. */
+smart_status smart_ang2pix(int nside, const double *ra_deg, const double *dec_deg,
+                           int64_t n, int64_t *pix, void *cuda_stream);
+
+/* vec[3k..3k+2] = unit vector of the centre of RING pixel pix[k] (f64). */
+smart_status smart_pix2vec(int nside, const int64_t *pix, int64_t n, double *vec,
+                           void *cuda_stream);
+
+/* Host helper: the chord^2 threshold T = 4 sin^2(theta_ap/2) the library
+   uses for theta_ap given in arcmin. */
+double smart_chord2(double theta_ap_arcmin);
+
+/* ---- inspection (tests, diagnostics) ------------------------------- */
+
+/*
+ * Copy the sorted catalogue out: perm[i] = input index of the galaxy at
+ * sorted position i, pix[i] = its pixel (both n entries), offsets[p] =
+ * sorted position of the first galaxy of pixel p (12 nside_bin^2 + 1
+ * entries).  Device pointers; any may be NULL.
+ */
+smart_status smart_get_catalog(smart_ctx *ctx, int64_t *perm, int64_t *pix, int64_t *offsets);
+
+/* Copy the binned map out (full-sky arrays at nside_bin). */
+smart_status smart_get_binned(smart_ctx *ctx, float *G1, float *G2, float *W,
+                              float *S2, int32_t *n_p);
+
+/* Number of member tests that fell inside the float32 guard band and were
+   decided in float64 by the last map call (host value; syncs the stream). */
+int64_t smart_last_fp64_decisions(smart_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMART_H */

@@ -513,12 +513,22 @@ int64_t orc_query_disc_all(int64_t nside, const double *r0, double T,
  * per centre: SE = sum Q (G1 cos2psi + G2 sin2psi), SB, SV = sum Q^2 S2,
  * SW = sum W, N = sum n.
  */
-void orc_aperture_pixels(int64_t n0, const double *c, int64_t nside_bin,
-                         const double *G1, const double *G2, const double *W,
-                         const double *S2, const int64_t *np,
-                         int kind, double xc, double theta_ap,
-                         double *SE, double *SB, double *SV, double *SW,
-                         int64_t *N, int64_t *NPIX)
+static double rd(const void *a, int f32, int64_t p)
+{
+    return f32 ? (double)((const float *)a)[p] : ((const double *)a)[p];
+}
+
+static int64_t rn(const void *a, int f32, int64_t p)
+{
+    return f32 ? (int64_t)((const int32_t *)a)[p] : ((const int64_t *)a)[p];
+}
+
+static void aperture_pixels_impl(int64_t n0, const double *c, int64_t nside_bin,
+                                 const void *G1, const void *G2, const void *W,
+                                 const void *S2, const void *np, int f32,
+                                 int kind, double xc, double theta_ap,
+                                 double *SE, double *SB, double *SV, double *SW,
+                                 int64_t *N, int64_t *NPIX)
 {
     orc_cfg cfg;
     cfg.kind = kind;
@@ -551,17 +561,41 @@ void orc_aperture_pixels(int64_t n0, const double *c, int64_t nside_bin,
                 double nh[3] = {-z * cp, -z * sp, rho};
                 double q, c2, s2;
                 if (!aperture_term(&cfg, r0, v, eh, nh, &q, &c2, &s2)) continue;
-                se += q * (G1[p] * c2 + G2[p] * s2);
-                sb += q * (-G1[p] * s2 + G2[p] * c2);
-                sv += q * q * S2[p];
-                sw += W[p];
-                cnt += np[p];
+                double g1 = rd(G1, f32, p), g2 = rd(G2, f32, p);
+                se += q * (g1 * c2 + g2 * s2);
+                sb += q * (-g1 * s2 + g2 * c2);
+                sv += q * q * rd(S2, f32, p);
+                sw += rd(W, f32, p);
+                cnt += rn(np, f32, p);
             }
             SE[t] = se; SB[t] = sb; SV[t] = sv; SW[t] = sw; N[t] = cnt;
             if (NPIX) NPIX[t] = m;
         }
         free(buf);
     }
+}
+
+void orc_aperture_pixels(int64_t n0, const double *c, int64_t nside_bin,
+                         const double *G1, const double *G2, const double *W,
+                         const double *S2, const int64_t *np,
+                         int kind, double xc, double theta_ap,
+                         double *SE, double *SB, double *SV, double *SW,
+                         int64_t *N, int64_t *NPIX)
+{
+    aperture_pixels_impl(n0, c, nside_bin, G1, G2, W, S2, np, 0, kind, xc, theta_ap,
+                         SE, SB, SV, SW, N, NPIX);
+}
+
+/* same, reading float32 sums and int32 counts (as the GPU path stores them) */
+void orc_aperture_pixels_f32(int64_t n0, const double *c, int64_t nside_bin,
+                             const float *G1, const float *G2, const float *W,
+                             const float *S2, const int32_t *np,
+                             int kind, double xc, double theta_ap,
+                             double *SE, double *SB, double *SV, double *SW,
+                             int64_t *N, int64_t *NPIX)
+{
+    aperture_pixels_impl(n0, c, nside_bin, G1, G2, W, S2, np, 1, kind, xc, theta_ap,
+                         SE, SB, SV, SW, N, NPIX);
 }
 
 /*

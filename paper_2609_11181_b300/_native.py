@@ -1,0 +1,72 @@
+"""ctypes loader for the SMART CUDA library (``_lib/libsmart.so``).
+
+There is no fallback: if the library is missing or fails to load, importing
+the package's GPU API raises.  Build it with
+``python -m paper_2609_11181_b300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsmart.so")
+
+STATUS = {0: "SMART_OK", 1: "SMART_E_ARG", 2: "SMART_E_NOMEM", 3: "SMART_E_CUDA", 4: "SMART_E_STATE",
+          5: "SMART_E_TIMEOUT", 6: "SMART_E_OVERFLOW", 7: "SMART_E_INTERNAL"}
+
+FILTER_POLY = 1
+FILTER_SCHIRMER = 2
+
+
+class SmartFilter(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("xc", ctypes.c_double)]
+
+
+class SmartMaps(ctypes.Structure):
+    _fields_ = [("sum_w", ctypes.c_void_p), ("map_e", ctypes.c_void_p), ("map_b", ctypes.c_void_p),
+                ("var", ctypes.c_void_p), ("count", ctypes.c_void_p), ("members", ctypes.c_void_p)]
+
+
+# every symbol declared in include/smart.h, with its ctypes signature
+_VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+SIGNATURES = {
+    "smart_create": (_I32, [_I32, ctypes.POINTER(SmartFilter), _D, _I32, _VP, ctypes.POINTER(_VP)]),
+    "smart_destroy": (None, [_VP]),
+    "smart_sync": (_I32, [_VP, _D]),
+    "smart_last_error": (ctypes.c_char_p, [_VP]),
+    "smart_set_targets": (_I32, [_VP, _VP, _I64]),
+    "smart_bin_galaxies": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _I64]),
+    "smart_set_binned": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smart_map_bruteforce": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
+    "smart_map_pixel": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
+    "smart_ang2pix": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP]),
+    "smart_pix2vec": (_I32, [_I32, _VP, _I64, _VP, _VP]),
+    "smart_chord2": (_D, [_D]),
+    "smart_get_catalog": (_I32, [_VP, _VP, _VP, _VP]),
+    "smart_get_binned": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smart_last_fp64_decisions": (_I64, [_VP]),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"SMART CUDA library not built: {LIB_PATH} is missing "
+                              "(run: python -m paper_2609_11181_b300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class SmartError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status

@@ -1,0 +1,189 @@
+"""Python binding of the SMART C ABI (argument marshalling only).
+
+Every step of the computation runs in the CUDA library; this module checks
+tensor devices/dtypes, passes raw device pointers and the current torch
+stream, and turns status codes into exceptions.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _native as N
+from ._native import SmartError
+
+ARCMIN = math.pi / 10800.0
+
+
+def _stream_handle(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None, dtype: torch.dtype, name: str, n: int | None = None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def chord2(theta_ap_arcmin: float) -> float:
+    """T = 4 sin^2(theta_ap/2) as the library computes it (host helper)."""
+    return N.load().smart_chord2(float(theta_ap_arcmin))
+
+
+def ang2pix(nside: int, ra_deg: torch.Tensor, dec_deg: torch.Tensor) -> torch.Tensor:
+    n = ra_deg.numel()
+    out = torch.empty(n, dtype=torch.int64, device=ra_deg.device)
+    st = N.load().smart_ang2pix(nside, _ptr(ra_deg, torch.float64, "ra"), _ptr(dec_deg, torch.float64, "dec", n),
+                                n, _ptr(out, torch.int64, "pix"), _stream_handle())
+    if st:
+        raise SmartError(st, "smart_ang2pix")
+    return out
+
+
+def pix2vec(nside: int, pix: torch.Tensor) -> torch.Tensor:
+    n = pix.numel()
+    out = torch.empty((n, 3), dtype=torch.float64, device=pix.device)
+    st = N.load().smart_pix2vec(nside, _ptr(pix, torch.int64, "pix"), n, _ptr(out, torch.float64, "vec"),
+                                _stream_handle())
+    if st:
+        raise SmartError(st, "smart_pix2vec")
+    return out
+
+
+class Context:
+    """One aperture-mass problem: output grid, filter, aperture, bin grid."""
+
+    def __init__(self, nside_out: int, theta_ap_arcmin: float, filter: str = "poly", xc: float = 0.15,
+                 nside_bin: int | None = None, stream: torch.cuda.Stream | None = None):
+        self._lib = N.load()
+        kind = {"poly": N.FILTER_POLY, "schirmer": N.FILTER_SCHIRMER}[filter]
+        f = N.SmartFilter(kind, float(xc))
+        h = ctypes.c_void_p()
+        self._stream = stream
+        self.nside_out = int(nside_out)
+        self.nside_bin = int(nside_bin if nside_bin is not None else nside_out)
+        self.theta_ap_arcmin = float(theta_ap_arcmin)
+        self.filter = filter
+        self.xc = float(xc)
+        st = self._lib.smart_create(self.nside_out, ctypes.byref(f), self.theta_ap_arcmin, self.nside_bin,
+                                    _stream_handle(stream), ctypes.byref(h))
+        if st:
+            raise SmartError(st, "smart_create")
+        self._h = h
+        self._keep = []
+        self.n_targets = 0
+
+    # -- plumbing
+    def _check(self, st: int, what: str):
+        if st:
+            msg = self._lib.smart_last_error(self._h)
+            raise SmartError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.smart_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def npix_bin(self) -> int:
+        return 12 * self.nside_bin * self.nside_bin
+
+    # -- inputs
+    def set_targets(self, pix: torch.Tensor):
+        n = pix.numel()
+        self._check(self._lib.smart_set_targets(self._h, _ptr(pix, torch.int64, "targets"), n), "smart_set_targets")
+        self.n_targets = n
+
+    def bin_galaxies(self, ra_deg, dec_deg, e1, e2, w=None):
+        n = ra_deg.numel()
+        self._check(self._lib.smart_bin_galaxies(
+            self._h, _ptr(ra_deg, torch.float64, "ra", n), _ptr(dec_deg, torch.float64, "dec", n),
+            _ptr(e1, torch.float32, "e1", n), _ptr(e2, torch.float32, "e2", n),
+            _ptr(w, torch.float32, "w", n), n), "smart_bin_galaxies")
+
+    def set_binned(self, G1, G2, W, S2, n_p):
+        m = self.npix_bin
+        self._check(self._lib.smart_set_binned(
+            self._h, _ptr(G1, torch.float32, "G1", m), _ptr(G2, torch.float32, "G2", m),
+            _ptr(W, torch.float32, "W", m), _ptr(S2, torch.float32, "S2", m), _ptr(n_p, torch.int32, "n_p", m)),
+            "smart_set_binned")
+        self._keep = [G1, G2, W, S2, n_p]
+
+    # -- maps
+    def _out(self, out):
+        if out is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+            n = self.n_targets
+            out = dict(sum_w=torch.empty(n, dtype=torch.float64, device=dev),
+                       map_e=torch.empty(n, dtype=torch.float32, device=dev),
+                       map_b=torch.empty(n, dtype=torch.float32, device=dev),
+                       var=torch.empty(n, dtype=torch.float32, device=dev),
+                       count=torch.empty(n, dtype=torch.int64, device=dev),
+                       members=torch.empty(n, dtype=torch.int32, device=dev))
+        n = self.n_targets
+        m = N.SmartMaps(_ptr(out.get("sum_w"), torch.float64, "sum_w", n),
+                        _ptr(out.get("map_e"), torch.float32, "map_e", n),
+                        _ptr(out.get("map_b"), torch.float32, "map_b", n),
+                        _ptr(out.get("var"), torch.float32, "var", n),
+                        _ptr(out.get("count"), torch.int64, "count", n),
+                        _ptr(out.get("members"), torch.int32, "members", n))
+        return out, m
+
+    def map_pixel(self, out: dict | None = None) -> dict:
+        out, m = self._out(out)
+        self._check(self._lib.smart_map_pixel(self._h, ctypes.byref(m)), "smart_map_pixel")
+        return out
+
+    def map_bruteforce(self, out: dict | None = None) -> dict:
+        out, m = self._out(out)
+        self._check(self._lib.smart_map_bruteforce(self._h, ctypes.byref(m)), "smart_map_bruteforce")
+        return out
+
+    def sync(self, timeout_s: float = 0.0):
+        self._check(self._lib.smart_sync(self._h, float(timeout_s)), "smart_sync")
+
+    def fp64_decisions(self) -> int:
+        return int(self._lib.smart_last_fp64_decisions(self._h))
+
+    # -- inspection
+    def get_catalog(self, n: int):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        perm = torch.empty(n, dtype=torch.int64, device=dev)
+        pix = torch.empty(n, dtype=torch.int64, device=dev)
+        off = torch.empty(self.npix_bin + 1, dtype=torch.int64, device=dev)
+        self._check(self._lib.smart_get_catalog(self._h, _ptr(perm, torch.int64, "perm"),
+                                                _ptr(pix, torch.int64, "pix"), _ptr(off, torch.int64, "off")),
+                    "smart_get_catalog")
+        return perm, pix, off
+
+    def get_binned(self):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        m = self.npix_bin
+        G1, G2, W, S2 = (torch.empty(m, dtype=torch.float32, device=dev) for _ in range(4))
+        n_p = torch.empty(m, dtype=torch.int32, device=dev)
+        self._check(self._lib.smart_get_binned(self._h, *(_ptr(x, x.dtype, "b") for x in (G1, G2, W, S2, n_p))),
+                    "smart_get_binned")
+        return dict(G1=G1, G2=G2, W=W, S2=S2, n=n_p)

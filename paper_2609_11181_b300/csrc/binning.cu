@@ -1,0 +1,437 @@
+// binning.cu -- catalogue partitioning by HEALPix pixel (Sect. 3.4 steps 1-3)
+// and per-pixel shear sums (Sect. 3.2 step 2) on the device.
+//
+//   1. pixel of every galaxy (float64, bit-exact with the definition);
+//   2. stable LSD radix sort of (pixel, input index), 8-bit digits;
+//   3. offset table = exclusive scan of the per-pixel counts;
+//   4. galaxy records permuted into sorted order (float32 offsets from the
+//      pixel centre for the aperture kernel, float64 ra/dec for exact
+//      re-decisions);
+//   5. per-pixel sums G1, G2, W, S2 and counts, accumulated in sorted order.
+#include <math.h>
+
+#include <algorithm>
+
+#include "smart_internal.cuh"
+
+namespace smart {
+
+static constexpr int RADIX_BITS = 8;
+static constexpr int RADIX = 1 << RADIX_BITS;
+static constexpr int SORT_THREADS = 256;
+static constexpr int SORT_ITEMS = 16;
+static constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;   // 4096 keys per tile
+static constexpr int SORT_WARPS = SORT_THREADS / 32;
+static constexpr int SCAN_THREADS = 256;
+static constexpr int SCAN_ITEMS = 8;
+static constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// ---------------------------------------------------------------- keys
+__global__ void k_keys(int64_t N, const double *__restrict__ ra, const double *__restrict__ dec, int64_t n,
+                       uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, int *__restrict__ invalid) {
+    const int64_t npix = 12 * N * N;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double a = ra[k], d = dec[k];
+        uint32_t key;
+        if (isfinite(a) && isfinite(d) && d >= -90.0 && d <= 90.0 && fabs(a) < 1e12) {
+            key = (uint32_t)ang2pix64(N, a, d);
+        } else {
+            key = (uint32_t)npix;             // sentinel bucket after every real pixel
+            atomicAdd(invalid, 1);
+        }
+        keys[k] = key;
+        vals[k] = (uint32_t)k;
+    }
+}
+
+// ------------------------------------------------------- radix passes
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                            int64_t ntiles, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t i = base + r * SORT_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter.  Warp w of the tile owns the contiguous items
+// [w*512, (w+1)*512) and walks them in 16 rounds of 32 consecutive items, so
+// the ranking order (warp, round, lane) is the input order.
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                               const uint32_t *__restrict__ vin,
+                                                               uint32_t *__restrict__ kout,
+                                                               uint32_t *__restrict__ vout, int64_t n, int shift,
+                                                               int64_t ntiles, const uint32_t *__restrict__ hscan) {
+    __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
+    __shared__ uint32_t tbase[RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = lane; d < RADIX; d += 32) wcnt[warp][d] = 0;
+    tbase[threadIdx.x] = hscan[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * (32 * SORT_ITEMS);
+    uint32_t key[SORT_ITEMS], val[SORT_ITEMS], rank[SORT_ITEMS];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool ok = i < n;
+        const unsigned valid = __ballot_sync(0xffffffffu, ok);
+        key[r] = ok ? kin[i] : 0u;
+        val[r] = ok ? vin[i] : 0u;
+        const uint32_t d = (key[r] >> shift) & (RADIX - 1);
+        rank[r] = 0;
+        if (ok) {
+            const unsigned peers = __match_any_sync(valid, d);
+            const uint32_t before = wcnt[warp][d];
+            rank[r] = before + __popc(peers & lt);
+            __syncwarp(valid);
+            if ((peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps for each digit (thread = digit)
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (key[r] >> shift) & (RADIX - 1);
+            const uint32_t pos = tbase[d] + wcnt[warp][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// ------------------------------------------------------------- scan
+// exclusive scan of uint32/int32 counts (totals < 2^31), reduce-then-scan
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict__ in, int32_t *__restrict__ out,
+                                                           int64_t n, int32_t *__restrict__ sums) {
+    __shared__ int32_t ws[SCAN_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k;
+        v[k] = i < n ? (int32_t)in[i] : 0;
+        acc += v[k];
+    }
+    // inclusive scan of per-thread totals across the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t s = lane < SCAN_THREADS / 32 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCAN_THREADS / 32) ws[lane] = s;
+    }
+    __syncthreads();
+    int32_t run = x - acc + (warp > 0 ? ws[warp - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t i = base + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == SCAN_THREADS - 1 && sums) sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(int32_t *__restrict__ out, int64_t n, const int32_t *__restrict__ sums) {
+    const int64_t i = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x;
+    const int32_t s = sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        const int64_t j = i + (int64_t)k * SCAN_THREADS;
+        if (j < n) out[j] += s;
+    }
+}
+
+template <typename T>
+static smart_status scan_impl(smart_ctx *ctx, const T *in, int32_t *out, int64_t n, int32_t *tmp, int64_t tmp_cap) {
+    if (n <= 0) return SMART_OK;
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 1) {
+        k_scan_tile<T><<<1, SCAN_THREADS, 0, ctx->stream>>>(in, out, n, nullptr);
+        return check_cuda(ctx, cudaGetLastError(), "scan");
+    }
+    if (nb + 1 > tmp_cap) return fail(ctx, SMART_E_INTERNAL, "scan scratch too small");
+    int32_t *sums = tmp;
+    k_scan_tile<T><<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, out, n, sums);
+    smart_status st = check_cuda(ctx, cudaGetLastError(), "scan tiles");
+    if (st != SMART_OK) return st;
+    st = scan_impl<int32_t>(ctx, sums, sums, nb, tmp + nb, tmp_cap - nb);
+    if (st != SMART_OK) return st;
+    k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(out, n, sums);
+    return check_cuda(ctx, cudaGetLastError(), "scan add");
+}
+
+static int64_t scan_scratch(int64_t n) {
+    int64_t s = 0;
+    while (n > SCAN_TILE) {
+        n = (n + SCAN_TILE - 1) / SCAN_TILE;
+        s += n + 1;
+    }
+    return s + 1;
+}
+
+// ------------------------------------------------ counts and offsets
+// keys are sorted: the first element of each run of equal keys measures the
+// run and stores its length
+__global__ void k_run_counts(const uint32_t *__restrict__ keys, int64_t n, uint32_t npix1,
+                             int32_t *__restrict__ counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        if (i > 0 && keys[i - 1] == k) continue;
+        int64_t j = i + 1;
+        while (j < n && keys[j] == k) ++j;
+        if (k < npix1) counts[k] = (int32_t)(j - i);
+    }
+}
+
+// per-ring latitude in degrees (for galaxy offsets from their pixel centre)
+__global__ void k_ring_lat(int64_t N, double *__restrict__ lat_deg) {
+    const int64_t i = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i > 4 * N - 1) return;
+    const RingGeom g = ring_geom(N, i);
+    lat_deg[i] = atan2(g.z, g.rho) * (180.0 / SMART_PI);
+}
+
+// records in sorted order
+__global__ void k_records(int64_t N, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                          int64_t n, const double *__restrict__ ra, const double *__restrict__ dec,
+                          const float *__restrict__ e1, const float *__restrict__ e2, const float *__restrict__ w,
+                          const double *__restrict__ lat_deg, float4 *__restrict__ geo, float4 *__restrict__ sh,
+                          double2 *__restrict__ radec) {
+    const int64_t npix = 12 * N * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = keys[i];
+        const uint32_t g = vals[i];
+        const double a = ra[g], d = dec[g];
+        const float ww = w ? w[g] : 1.0f;
+        const float x1 = e1[g], x2 = e2[g];
+        float4 gr = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((int64_t)p < npix) {
+            const RingPix rp = pix_to_ring(N, p);
+            const double cphi = 90.0 * ring_phi_quarter(N, rp.ring, rp.j);   // centre azimuth, degrees
+            double da = fmod(a - cphi, 360.0);
+            if (da > 180.0) da -= 360.0;
+            if (da <= -180.0) da += 360.0;
+            const double dd = d - lat_deg[rp.ring];
+            float sd, cd;
+            sincospif((float)(d / 180.0), &sd, &cd);
+            gr = make_float4((float)(dd * (SMART_PI / 180.0)), (float)(da * (SMART_PI / 180.0)), sd, cd);
+        }
+        geo[i] = gr;
+        sh[i] = make_float4(ww * x1, ww * x2, ww, ww * ww * (x1 * x1 + x2 * x2));
+        radec[i] = make_double2(a, d);
+    }
+}
+
+// per-pixel sums in sorted order (one thread per pixel)
+__global__ void k_pixel_sums(const int32_t *__restrict__ off, int64_t npix, const float4 *__restrict__ sh,
+                             float *__restrict__ G1, float *__restrict__ G2, float *__restrict__ W,
+                             float *__restrict__ S2, int32_t *__restrict__ np) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = off[p], b = off[p + 1];
+        float g1 = 0.f, g2 = 0.f, ww = 0.f, s2 = 0.f;
+        for (int32_t k = a; k < b; ++k) {
+            const float4 v = sh[k];
+            g1 += v.x;
+            g2 += v.y;
+            ww += v.z;
+            s2 += v.w;
+        }
+        G1[p] = g1;
+        G2[p] = g2;
+        W[p] = ww;
+        S2[p] = s2;
+        np[p] = b - a;
+    }
+}
+
+static smart_status ensure_gal_buffers(smart_ctx *c, int64_t n) {
+    if (n <= c->cap_gal && c->keys) return SMART_OK;
+    cudaStreamSynchronize(c->stream);
+    void **bufs[] = {(void **)&c->keys, (void **)&c->keys_alt, (void **)&c->vals, (void **)&c->vals_alt,
+                     (void **)&c->rec_geo, (void **)&c->rec_shear, (void **)&c->rec_radec};
+    const size_t elem[] = {4, 4, 4, 4, 16, 16, 16};
+    for (void **b : bufs) {
+        if (*b) cudaFree(*b);
+        *b = nullptr;
+    }
+    c->cap_gal = 0;
+    const int64_t cap = std::max<int64_t>(n, 1);
+    for (int k = 0; k < 7; ++k)
+        if (cudaMalloc(bufs[k], (size_t)cap * elem[k]) != cudaSuccess)
+            return fail(c, SMART_E_NOMEM, "cudaMalloc(galaxy buffers) failed");
+    c->cap_gal = cap;
+    return SMART_OK;
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 148 * 32));
+}
+
+smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out, int64_t n) {
+    smart_status st = ensure_alloc(ctx, (void **)&ctx->scan_tmp, ctx->cap_scan, scan_scratch(n), sizeof(int64_t), "scan scratch");
+    if (st != SMART_OK) return st;
+    return scan_impl<int32_t>(ctx, in, out, n, (int32_t *)ctx->scan_tmp, ctx->cap_scan * 2);
+}
+
+}  // namespace smart
+
+using namespace smart;
+
+extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const double *dec, const float *e1,
+                                           const float *e2, const float *w, int64_t n) {
+    if (!c) return SMART_E_ARG;
+    if (n < 0 || (n > 0 && (!ra || !dec || !e1 || !e2))) return fail(c, SMART_E_ARG, "smart_bin_galaxies: bad pointer or size");
+    if (n >= ((int64_t)1 << 31) - 1) return fail(c, SMART_E_OVERFLOW, "smart_bin_galaxies: more than 2^31-2 galaxies");
+    const int64_t N = c->nside_bin;
+    const int64_t npix = npix_of(N);
+    int bits = 0;
+    while (((int64_t)1 << bits) <= npix) ++bits;          // keys go up to npix (sentinel)
+    smart_status st = ensure_gal_buffers(c, n);
+    if (st != SMART_OK) return st;
+    if (!c->offsets) {
+        if (cudaMalloc(&c->offsets, (size_t)(npix + 1) * sizeof(int32_t)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(offsets) failed");
+        if (cudaMalloc(&c->own_binned, (size_t)4 * npix * sizeof(float)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(binned) failed");
+        if (cudaMalloc(&c->own_np, (size_t)(npix + 1) * sizeof(int32_t)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(counts) failed");
+        if (cudaMalloc(&c->ring_lat, (size_t)(4 * N) * sizeof(double)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(ring lat) failed");
+        if (cudaMalloc(&c->d_invalid, sizeof(int)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(flag) failed");
+        k_ring_lat<<<(unsigned)((4 * N + 127) / 128), 128, 0, c->stream>>>(N, c->ring_lat);
+    }
+    const int64_t ntiles = std::max<int64_t>(1, (n + SORT_TILE - 1) / SORT_TILE);
+    st = ensure_alloc(c, (void **)&c->hist, c->cap_hist, (int64_t)RADIX * ntiles, sizeof(uint32_t), "radix histogram");
+    if (st != SMART_OK) return st;
+    st = ensure_alloc(c, (void **)&c->hist_scan, c->cap_hist_scan, (int64_t)RADIX * ntiles, sizeof(int32_t), "radix scan");
+    if (st != SMART_OK) return st;
+    int32_t *hscan = c->hist_scan;
+    const int64_t scan_need = std::max(scan_scratch(npix + 1), scan_scratch((int64_t)RADIX * ntiles));
+    st = ensure_alloc(c, (void **)&c->scan_tmp, c->cap_scan, scan_need, sizeof(int64_t), "scan scratch");
+    if (st != SMART_OK) return st;
+
+    cudaStream_t s = c->stream;
+    cudaMemsetAsync(c->d_invalid, 0, sizeof(int), s);
+    if (n > 0) {
+        k_keys<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, c->keys, c->vals, c->d_invalid);
+        if ((st = check_cuda(c, cudaGetLastError(), "k_keys")) != SMART_OK) return st;
+        uint32_t *ki = c->keys, *ko = c->keys_alt, *vi = c->vals, *vo = c->vals_alt;
+        for (int shift = 0; shift < bits; shift += RADIX_BITS) {
+            k_radix_hist<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, n, shift, ntiles, c->hist);
+            st = scan_impl<uint32_t>(c, c->hist, hscan, (int64_t)RADIX * ntiles, (int32_t *)c->scan_tmp, c->cap_scan * 2);
+            if (st != SMART_OK) return st;
+            k_radix_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, (const uint32_t *)hscan);
+            if ((st = check_cuda(c, cudaGetLastError(), "k_radix_scatter")) != SMART_OK) return st;
+            std::swap(ki, ko);
+            std::swap(vi, vo);
+        }
+        if (ki != c->keys) {          // keep the sorted arrays in keys/vals
+            std::swap(c->keys, c->keys_alt);
+            std::swap(c->vals, c->vals_alt);
+        }
+    }
+    // counts per pixel (+ the sentinel bucket at npix), then offsets
+    int32_t *counts = c->own_np;     // reused: the per-pixel counts are exactly n_p
+    cudaMemsetAsync(counts, 0, (size_t)(npix + 1) * sizeof(int32_t), s);
+    if (n > 0) {
+        k_run_counts<<<grid_for(n, 256), 256, 0, s>>>(c->keys, n, (uint32_t)npix, counts);
+        if ((st = check_cuda(c, cudaGetLastError(), "k_run_counts")) != SMART_OK) return st;
+    }
+    // offsets[0..npix] = exclusive scan of counts[0..npix] (counts[npix] = 0)
+    st = scan_impl<int32_t>(c, counts, c->offsets, npix + 1, (int32_t *)c->scan_tmp, c->cap_scan * 2);
+    if (st != SMART_OK) return st;
+    if (n > 0) {
+        k_records<<<grid_for(n, 256), 256, 0, s>>>(N, c->keys, c->vals, n, ra, dec, e1, e2, w, c->ring_lat,
+                                                   c->rec_geo, c->rec_shear, c->rec_radec);
+        if ((st = check_cuda(c, cudaGetLastError(), "k_records")) != SMART_OK) return st;
+    }
+    float *B = c->own_binned;
+    k_pixel_sums<<<grid_for(npix, 256), 256, 0, s>>>(c->offsets, npix, c->rec_shear, B, B + npix, B + 2 * npix,
+                                                     B + 3 * npix, c->own_np);
+    if ((st = check_cuda(c, cudaGetLastError(), "k_pixel_sums")) != SMART_OK) return st;
+    c->G1 = B;
+    c->G2 = B + npix;
+    c->W = B + 2 * npix;
+    c->S2 = B + 3 * npix;
+    c->NP = c->own_np;
+    c->have_binned = true;
+    c->have_catalog = true;
+    c->n_gal = n;
+    int inv = 0;
+    cudaMemcpyAsync(&inv, c->d_invalid, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if ((st = check_cuda(c, cudaStreamSynchronize(s), "smart_bin_galaxies")) != SMART_OK) return st;
+    if (inv) {
+        c->have_catalog = false;
+        c->have_binned = false;
+        return fail(c, SMART_E_ARG, "smart_bin_galaxies: " + std::to_string(inv) +
+                                        " galaxies with non-finite ra/dec or |dec| > 90");
+    }
+    return SMART_OK;
+}
+
+__global__ void k_copy_catalog(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                               int64_t *__restrict__ perm, int64_t *__restrict__ pix) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (perm) perm[i] = vals[i];
+        if (pix) pix[i] = keys[i];
+    }
+}
+
+__global__ void k_copy_offsets(const int32_t *__restrict__ off, int64_t m, int64_t *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = off[i];
+}
+
+extern "C" smart_status smart_get_catalog(smart_ctx *c, int64_t *perm, int64_t *pix, int64_t *offsets) {
+    if (!c) return SMART_E_ARG;
+    if (!c->have_catalog) return fail(c, SMART_E_STATE, "smart_get_catalog: no catalogue binned");
+    const int64_t npix = npix_of(c->nside_bin);
+    if ((perm || pix) && c->n_gal > 0)
+        k_copy_catalog<<<grid_for(c->n_gal, 256), 256, 0, c->stream>>>(c->keys, c->vals, c->n_gal, perm, pix);
+    if (offsets) k_copy_offsets<<<grid_for(npix + 1, 256), 256, 0, c->stream>>>(c->offsets, npix + 1, offsets);
+    return check_cuda(c, cudaGetLastError(), "smart_get_catalog");
+}
+
+extern "C" smart_status smart_get_binned(smart_ctx *c, float *G1, float *G2, float *W, float *S2, int32_t *n_p) {
+    if (!c) return SMART_E_ARG;
+    if (!c->have_binned) return fail(c, SMART_E_STATE, "smart_get_binned: no binned map");
+    const size_t npix = (size_t)npix_of(c->nside_bin);
+    const void *src[5] = {c->G1, c->G2, c->W, c->S2, c->NP};
+    void *dst[5] = {G1, G2, W, S2, n_p};
+    for (int k = 0; k < 5; ++k)
+        if (dst[k]) {
+            smart_status st = check_cuda(c, cudaMemcpyAsync(dst[k], src[k], npix * 4, cudaMemcpyDeviceToDevice, c->stream), "smart_get_binned");
+            if (st != SMART_OK) return st;
+        }
+    return SMART_OK;
+}

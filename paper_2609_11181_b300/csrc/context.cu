@@ -1,0 +1,159 @@
+// context.cu -- lifetime, error reporting and input registration of a SMART
+// context (the C ABI declared in include/smart.h).
+#include <math.h>
+
+#include <chrono>
+#include <thread>
+
+#include "smart_internal.cuh"
+
+namespace smart {
+
+smart_status fail(smart_ctx *ctx, smart_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+smart_status check_cuda(smart_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SMART_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? SMART_E_NOMEM : SMART_E_CUDA, m);
+}
+
+// grow-only device buffer: reallocates when `need` elements exceed `cap`
+smart_status ensure_alloc(smart_ctx *ctx, void **p, int64_t &cap, int64_t need, size_t elem, const char *what) {
+    if (need <= cap && *p) return SMART_OK;
+    if (*p) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(*p);
+        *p = nullptr;
+        cap = 0;
+    }
+    const int64_t n = need > 0 ? need : 1;
+    cudaError_t e = cudaMalloc(p, (size_t)n * elem);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, SMART_E_NOMEM, std::string("cudaMalloc(") + what + ") failed");
+    }
+    cap = n;
+    return SMART_OK;
+}
+
+}  // namespace smart
+
+using namespace smart;
+
+static bool nside_ok(int nside) { return nside >= 1 && nside <= 8192 && (nside & (nside - 1)) == 0; }
+
+extern "C" smart_status smart_create(int nside_out, const smart_filter *filter, double theta_ap_arcmin,
+                                     int nside_bin, void *cuda_stream, smart_ctx **out) {
+    if (!out) return SMART_E_ARG;
+    *out = nullptr;
+    if (!nside_ok(nside_out) || !nside_ok(nside_bin) || !filter) return SMART_E_ARG;
+    if (filter->kind != SMART_FILTER_POLY && filter->kind != SMART_FILTER_SCHIRMER) return SMART_E_ARG;
+    if (filter->kind == SMART_FILTER_SCHIRMER && !(filter->xc > 0.0 && filter->xc < 10.0)) return SMART_E_ARG;
+    if (!(theta_ap_arcmin > 0.0) || !(theta_ap_arcmin <= 3600.0)) return SMART_E_ARG;
+    smart_ctx *c = new (std::nothrow) smart_ctx();
+    if (!c) return SMART_E_NOMEM;
+    c->nside_out = nside_out;
+    c->nside_bin = nside_bin;
+    c->filter_kind = filter->kind;
+    c->xc = filter->kind == SMART_FILTER_SCHIRMER ? filter->xc : 0.15;
+    c->theta_ap = theta_ap_arcmin * SMART_PI / 10800.0;
+    c->T = smart_chord2(theta_ap_arcmin);
+    c->area = 2.0 * SMART_PI * (0.5 * c->T);     // 2 pi (1 - cos theta_ap) = pi T
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaMalloc(&c->d_fp64_count, sizeof(unsigned long long)) != cudaSuccess) {
+        delete c;
+        return SMART_E_NOMEM;
+    }
+    *out = c;
+    return SMART_OK;
+}
+
+extern "C" void smart_destroy(smart_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    void *bufs[] = {c->targets, c->rp_pix, c->rp_gal, c->rp_pix_cnt, c->rp_gal_cnt, c->own_binned,
+                    c->own_np, c->keys, c->keys_alt, c->vals, c->vals_alt, c->offsets, c->rec_geo,
+                    c->rec_shear, c->rec_radec, c->hist, c->hist_scan, c->scan_tmp, c->ring_lat, c->d_invalid,
+                    c->d_fp64_count};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+}
+
+extern "C" const char *smart_last_error(const smart_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" smart_status smart_sync(smart_ctx *c, double timeout_s) {
+    if (!c) return SMART_E_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(c->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return check_cuda(c, e, "smart_sync");
+        if (timeout_s > 0) {
+            double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (dt > timeout_s) return fail(c, SMART_E_TIMEOUT, "smart_sync: deadline passed");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return SMART_OK;
+}
+
+__global__ void k_check_targets(const int64_t *__restrict__ t, int64_t n, int64_t npix, int *__restrict__ bad) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t[k];
+        if (p < 0 || p >= npix || (k > 0 && t[k - 1] >= p)) atomicExch(bad, 1);
+    }
+}
+
+extern "C" smart_status smart_set_targets(smart_ctx *c, const int64_t *pix, int64_t n) {
+    if (!c) return SMART_E_ARG;
+    if (n < 0 || (n > 0 && !pix)) return fail(c, SMART_E_ARG, "smart_set_targets: bad pointer or size");
+    if (n > ((int64_t)1 << 31)) return fail(c, SMART_E_OVERFLOW, "smart_set_targets: more than 2^31 targets");
+    smart_status st = ensure_alloc(c, (void **)&c->targets, c->cap_targets, n, sizeof(int64_t), "targets");
+    if (st != SMART_OK) return st;
+    c->n_targets = n;
+    if (n == 0) return SMART_OK;
+    st = check_cuda(c, cudaMemcpyAsync(c->targets, pix, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream),
+                    "copy targets");
+    if (st != SMART_OK) return st;
+    // validate range and ordering once (a small synchronous check)
+    int *bad = nullptr;
+    if (cudaMallocAsync(&bad, sizeof(int), c->stream) != cudaSuccess) return fail(c, SMART_E_NOMEM, "flag alloc");
+    cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    k_check_targets<<<blocks, 256, 0, c->stream>>>(c->targets, n, npix_of(c->nside_out), bad);
+    int hb = 0;
+    cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(bad, c->stream);
+    st = check_cuda(c, cudaStreamSynchronize(c->stream), "validate targets");
+    if (st != SMART_OK) return st;
+    if (hb) {
+        c->n_targets = 0;
+        return fail(c, SMART_E_ARG, "smart_set_targets: pixels must be unique, ascending and in [0, 12 nside_out^2)");
+    }
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_set_binned(smart_ctx *c, const float *G1, const float *G2, const float *W,
+                                         const float *S2, const int32_t *n_p) {
+    if (!c) return SMART_E_ARG;
+    if (!G1 || !G2 || !W || !S2 || !n_p) return fail(c, SMART_E_ARG, "smart_set_binned: null pointer");
+    c->G1 = G1;
+    c->G2 = G2;
+    c->W = W;
+    c->S2 = S2;
+    c->NP = n_p;
+    c->have_binned = true;
+    return SMART_OK;
+}
+
+extern "C" int64_t smart_last_fp64_decisions(smart_ctx *c) {
+    if (!c) return -1;
+    unsigned long long h = 0;
+    cudaMemcpyAsync(&h, c->d_fp64_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return (int64_t)h;
+}

@@ -131,10 +131,11 @@ def halos_poisson(density_per_deg2: float, area_deg2: float, ra0_deg, dec0_deg, 
     return halos_uniform(k, ra0_deg, dec0_deg, radius, gen, te_lo, te_hi, log=True)
 
 
-def sis_shear(ra_deg, dec_deg, halos: Halos, r_trunc: float, chunk: int = 1 << 21):
+def sis_shear(ra_deg, dec_deg, halos: Halos, r_trunc: float, chunk: int = 1 << 21, inner_cut: bool = True):
     """Summed SIS shear (gamma_1, gamma_2) in the local (East, North) basis.
 
-    gamma_t = theta_E / (2 theta) for 0 < theta <= r_trunc.  The orientation
+    gamma_t = theta_E / (2 theta) for 0 < theta <= r_trunc; with inner_cut
+    the strong-lensing core theta < theta_E is held at gamma_t = 1/2.  The orientation
     uses the great-circle bearing b of the halo seen from the point (from
     North through East): gamma_1 = gamma_t cos 2b, gamma_2 = -gamma_t sin 2b,
     so a point East of a halo is stretched North-South (gamma_1 < 0).
@@ -190,8 +191,8 @@ def sis_shear(ra_deg, dec_deg, halos: Halos, r_trunc: float, chunk: int = 1 << 2
         valid &= cosd >= cos_tr
         theta = torch.acos(torch.clamp(cosd, -1.0, 1.0))
         valid &= theta > 0
-        gt = torch.where(valid, hte[ci] / (2.0 * torch.clamp(theta, min=1e-30)),
-                         torch.zeros_like(theta))
+        th_eff = torch.maximum(theta, hte[ci]) if inner_cut else torch.clamp(theta, min=1e-30)
+        gt = torch.where(valid, hte[ci] / (2.0 * th_eff), torch.zeros_like(theta))
         a = torch.deg2rad(ra)[:, None]
         d = torch.deg2rad(dec)[:, None]
         da = ha[ci] - a
