@@ -169,10 +169,11 @@ def cpu_baseline_pixel(wl, budget_s=15.0, seed=0):
         r = oracle.aperture_pixels_f32(cv, wl.nside, *G, kind, th)
         return time.perf_counter() - t0, int(r["NPIX"].sum()), s.size
 
-    dt, pairs, m = run(max(64, cores * 8))
-    per = dt / max(m, 1)
-    m2 = int(min(tg.size, max(m, budget_s / max(per, 1e-9))))
-    dt, pairs, m = run(m2)
+    m = max(256, cores * 64)
+    dt, pairs, m = run(m)
+    while dt < 0.25 * budget_s and m < tg.size:          # grow until the timing is meaningful
+        m = int(min(tg.size, m * max(2.0, 0.5 * budget_s / max(dt, 1e-3))))
+        dt, pairs, m = run(m)
     return {"value": pairs / dt / 1e9, "unit": "Gpair/s", "cores": cores, "kind": "oracle",
             "sample": f"{m} random targets of {tg.size} (float64 oracle, OpenMP over targets), {pairs} pairs, "
                       f"{dt:.1f} s"}, pairs, dt, m

@@ -318,16 +318,18 @@ static int aperture_term(const orc_cfg *cfg, const double *r0, const double *p,
             / (cfg->theta_ap * cfg->theta_ap);
     /* direction from the point towards the centre in the point's tangent
        plane; the paper's tan(psi) equals -x/y (Sect. 2.3) */
+    if (ssq == 0.0) {
+        /* the point is the centre itself: psi is undefined (Sect. 2.3 gives
+           0/0), the point carries no tangential or cross shear */
+        *c2 = 0.0;
+        *s2 = 0.0;
+        return 1;
+    }
     double x = ehat[0] * r0[0] + ehat[1] * r0[1] + ehat[2] * r0[2];
     double y = nhat[0] * r0[0] + nhat[1] * r0[1] + nhat[2] * r0[2];
     double den = x * x + y * y;
-    if (den > 0.0) {
-        *c2 = (y * y - x * x) / den;            /* cos 2 psi */
-        *s2 = -2.0 * x * y / den;               /* sin 2 psi */
-    } else {                                    /* point at the centre */
-        *c2 = 0.0;
-        *s2 = 0.0;
-    }
+    *c2 = (y * y - x * x) / den;                /* cos 2 psi */
+    *s2 = -2.0 * x * y / den;                   /* sin 2 psi */
     return 1;
 }
 

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(128) k_map_pixel(const MapArgs a) {
             const float cc = fmaf(y, y, -xx);
             const float ss = -2.0f * x * y;
             const float Q = filter_Q<KIND>(a.f, s2);
-            const float w = sd2 > 0.f ? Q / sd2 : 0.f;
+            const float w = sd2 > 1e-30f ? Q / sd2 : 0.f;
             const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
             se = fmaf(w, fmaf(g1, cc, g2 * ss), se);
             sb = fmaf(w, fmaf(g2, cc, -g1 * ss), sb);

@@ -63,8 +63,11 @@ __global__ void k_ring_pairs(int64_t N0, int64_t N1, double theta_disc, double T
         const RingGeom g = ring_geom(N1, i);
         const double th = atan2(g.rho, g.z);
         if (th > th0 + theta_disc + margin) break;
-        const double dz = g.z - g0.z, dr = g.rho - g0.rho;
-        const double A = dz * dz + dr * dr;
+        // latitude difference: A = 4 sin^2(dlat/2) and C = sin(dlat) vanish
+        // exactly on the target's own ring (no cancellation of rho z0 - z rho0)
+        const double dlat = lat0 - atan2(g.z, g.rho);
+        const double sh = sin(0.5 * dlat);
+        const double A = 4.0 * sh * sh;
         if (A > Tdisc * (1.0 + 1e-9) + 1e-300) continue;   // no azimuth can reach the disc
         const double B = 4.0 * g.rho * g0.rho;
         const double dphi = 2.0 * SMART_PI / (double)g.nr;
@@ -96,12 +99,12 @@ __global__ void k_ring_pairs(int64_t N0, int64_t N1, double theta_disc, double T
         e.ring = (int)i;
         e.A = (float)A;
         e.B = (float)B;
-        e.C = (float)(g.rho * g0.z - g.z * g0.rho);
+        e.C = (float)sin(dlat);
         e.D = (float)(2.0 * g.z * g0.rho);
         e.dphi = (float)dphi;
         e.hw = (float)hw;
         e.mrho0 = (float)(-g0.rho);
-        e.dlat = (float)(lat0 - atan2(g.z, g.rho));
+        e.dlat = (float)dlat;
         e.rho0 = (float)g0.rho;
         e.z0 = (float)g0.z;
         e.pad0 = 0.f;

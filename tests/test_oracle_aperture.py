@@ -282,3 +282,22 @@ def test_pixel_mode_equals_snapped_brute_force(kind):
     np.testing.assert_array_equal(a["N"], s["N"])
     for k in ("SE", "SB", "SV", "SW"):
         np.testing.assert_allclose(a[k], s[k], rtol=1e-9, atol=1e-9 * np.abs(s[k]).max())
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_own_pixel_carries_no_shear(kind):
+    # a binned map whose only non-empty pixel is the target's own pixel: the
+    # position angle is undefined at the centre, so M_E = M_B = 0 exactly,
+    # while the weight and the noise term still count
+    nside = 256
+    npix = 12 * nside * nside
+    rng = np.random.default_rng(kind)
+    for p in rng.integers(0, npix, 25):
+        G1, G2, W, S2 = (np.zeros(npix) for _ in range(4))
+        n = np.zeros(npix, dtype=np.int64)
+        G1[p], G2[p], W[p], S2[p], n[p] = 3.0, -2.0, 5.0, 0.7, 5
+        r = oracle.map_pixels(oracle.pix2vec(nside, [p]), nside, G1, G2, W, S2, n, kind, 20 * ARCMIN)
+        assert r["SE"][0] == 0.0 and r["SB"][0] == 0.0
+        assert r["SW"][0] == 5.0 and r["N"][0] == 5
+        q0 = oracle.filter_q(kind, 0.0)[0] / (20 * ARCMIN) ** 2
+        assert r["SV"][0] == pytest.approx(q0 * q0 * 0.7, rel=1e-12, abs=1e-300)
