@@ -1,0 +1,193 @@
+// aperture_common.cuh -- shared pieces of the aperture-mass kernels.
+//
+// Per pair (target centre r0, point p) the geometry is reduced to float32
+// operations on constants of the ring pair (output ring of r0, bin ring of
+// p), computed once in float64 (geometry.cu):
+//   u   = azimuth of p - azimuth of r0       (from exact integer lattice offsets)
+//   h   = sin^2(u/2)
+//   s^2 = A + B h                            chord^2 between r0 and p
+//   x   = -rho0 sin u,  y = C + D h          direction p -> r0 in p's (East, North) basis
+//   x^2 + y^2 = sin^2 d,  cos 2psi = (y^2 - x^2)/sin^2 d,  sin 2psi = -2xy/sin^2 d
+// (the paper's tan psi of Sect. 2.3 equals -x/y; no atan2 is needed).
+// Membership s^2 <= T is decided in float32 outside a guard band of relative
+// width 4e-6 around T, and inside it by the float64 definition (unit
+// vectors from the same series sine/cosine as the float64 reference), so
+// member sets and counts are exact.
+#pragma once
+
+#include "smart_internal.cuh"
+
+namespace smart {
+
+constexpr int QTAB_BINS = 1024;      // filter table: cubic pieces on x = d / theta_ap in [0, 1]
+
+struct FilterArgs {
+    float inv_ap;      // 1 / theta_ap
+    float inv_ap2;     // 1 / theta_ap^2
+    float qnorm;       // poly: 6 / (pi theta_ap^2); table filters: 1 / theta_ap^2
+    float inv_xc;      // Schirmer 1 / xc
+    const float4 *qtab;  // QTAB_BINS cubic coefficients of q(x) (table filters)
+};
+
+struct MapArgs {
+    const int64_t *targets;
+    int64_t n;
+    int64_t N0, N1;
+    const RingPair *table;
+    const int *counts;
+    int kmax;
+    float Tlo, Thi;          // guard band around T (float32)
+    double T, area;
+    FilterArgs f;
+    // pixel-mode inputs
+    const float *G1, *G2, *W, *S2;
+    const int32_t *NP;
+    const int32_t *NPRE;     // exclusive prefix of NP over RING order (npix + 1)
+    // tiles of targets (pixel mode): first target of each tile, n_tiles + 1 entries
+    const int64_t *tiles;
+    int64_t n_tiles;
+    int *work;               // tile counter of the persistent launch
+    // brute-force inputs
+    const int32_t *offsets;
+    const float4 *geo, *shear;
+    const double2 *radec;
+    // outputs
+    double *sum_w;
+    float *map_e, *map_b, *var;
+    int64_t *count;
+    int32_t *members;
+    unsigned long long *fp64_count;
+};
+
+// great-circle separation^2 from the chord^2: d^2 = sum_n 2 s^(2n) / (n^2 C(2n,n))
+__device__ __forceinline__ float sep2_from_chord2(float s2) {
+    if (s2 > 0.05f) {
+        const float d = 2.0f * asinf(0.5f * sqrtf(s2));
+        return d * d;
+    }
+    return s2 * fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 3150.0f, 1.0f / 560.0f), 1.0f / 90.0f), 1.0f / 12.0f), 1.0f);
+}
+
+// q(x) from the cubic table: x in [0, 1], bins of width 1/QTAB_BINS
+__device__ __forceinline__ float qtab_eval(const float4 *tab, float x) {
+    const float f = x * (float)QTAB_BINS;
+    int i = (int)f;
+    i = min(max(i, 0), QTAB_BINS - 1);
+    const float t = f - (float)i;
+    const float4 c = tab[i];
+    return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+}
+
+// Q(d) from the chord^2.  Polynomial filter in closed form; the Schirmer
+// filter through its cubic table (tab points to a shared-memory copy).
+template <int KIND>
+__device__ __forceinline__ float filter_Q(const FilterArgs &f, const float4 *tab, float s2) {
+    const float d2 = sep2_from_chord2(s2);
+    if (KIND == SMART_FILTER_POLY) {
+        const float X2 = d2 * f.inv_ap2;
+        return f.qnorm * X2 * (1.0f - X2);
+    } else {
+        const float x = sqrtf(d2) * f.inv_ap;
+        return f.qnorm * qtab_eval(tab, x);
+    }
+}
+
+// sin u and sin^2(u/2): 2-term series for |u| <= 0.05 (rel. error < 1e-10),
+// 4-term for |u| <= 0.45 (< 2e-9), library sincos beyond
+__device__ __forceinline__ void sin_hav_narrow(float u, float &sinu, float &h) {
+    const float u2 = u * u;
+    sinu = u * fmaf(u2, -1.0f / 6.0f, 1.0f);
+    h = u2 * fmaf(u2, -1.0f / 48.0f, 0.25f);
+}
+
+__device__ __forceinline__ void sin_hav_small(float u, float &sinu, float &h) {
+    const float u2 = u * u;
+    sinu = u * fmaf(u2, fmaf(u2, fmaf(u2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+    h = u2 * fmaf(u2, fmaf(u2, fmaf(u2, -1.0f / 80640.0f, 1.0f / 1440.0f), -1.0f / 48.0f), 0.25f);
+}
+
+__device__ __forceinline__ void sin_hav_wide(float u, float &sinu, float &h) {
+    float sh, ch;
+    sincosf(0.5f * u, &sh, &ch);
+    sinu = 2.0f * sh * ch;
+    h = sh * sh;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+struct TargetRing {
+    int i0, j0, q0, s0, nr0;
+};
+
+__device__ __forceinline__ TargetRing target_ring(int64_t N0, int64_t pix) {
+    const RingPix rp = pix_to_ring(N0, pix);
+    TargetRing t;
+    t.i0 = rp.ring;
+    t.j0 = rp.j;
+    if (rp.ring < N0) {
+        t.q0 = rp.ring;
+        t.s0 = 1;
+    } else if (rp.ring <= 3 * N0) {
+        t.q0 = (int)N0;
+        t.s0 = ((rp.ring - N0) & 1) == 0 ? 1 : 0;
+    } else {
+        t.q0 = (int)(4 * N0 - rp.ring);
+        t.s0 = 1;
+    }
+    t.nr0 = 4 * t.q0;
+    return t;
+}
+
+// target position on the bin ring's azimuth lattice: X = (2 j0 + s0) q / (2 q0)
+// split as Xi + Xf with Xi integer and 0 <= Xf < 1 (exact integer arithmetic)
+__device__ __forceinline__ void lattice_position(const TargetRing &t, int q, int &Xi, float &Xf) {
+    if (q == t.q0) {
+        Xi = t.j0;
+        Xf = 0.5f * (float)t.s0;
+    } else {
+        const int64_t num = (int64_t)(2 * t.j0 + t.s0) * q;
+        const int64_t den = 2 * (int64_t)t.q0;
+        const int64_t qi = num / den;
+        Xi = (int)qi;
+        Xf = (float)(num - qi * den) / (float)den;
+    }
+}
+
+__device__ __forceinline__ void window(const RingPair &R, float fr, int &kl, int &kh) {
+    if (R.flags & RP_WHOLE) {
+        kl = (int)floorf(-0.5f * (float)R.nr - fr) + 1;
+        kh = kl + R.nr - 1;
+    } else {
+        kl = (int)ceilf(-fr - R.hw);
+        kh = (int)floorf(-fr + R.hw);
+    }
+}
+
+__device__ __forceinline__ void finalise(const MapArgs &a, int64_t t, float se, float cse, float sb, float csb,
+                                         float sv, float csv, float sw, float csw, int64_t cnt, int nmem) {
+    const double SW = (double)sw - (double)csw;
+    double me = 0.0, mb = 0.0, vv = 0.0;
+    if (SW > 0.0) {
+        const double nbar = SW / a.area;
+        me = ((double)se - (double)cse) / nbar;
+        mb = ((double)sb - (double)csb) / nbar;
+        vv = ((double)sv - (double)csv) / (2.0 * nbar * nbar);
+    }
+    if (a.sum_w) a.sum_w[t] = SW;
+    if (a.map_e) a.map_e[t] = (float)me;
+    if (a.map_b) a.map_b[t] = (float)mb;
+    if (a.var) a.var[t] = (float)vv;
+    if (a.count) a.count[t] = cnt;
+    if (a.members) a.members[t] = nmem;
+}
+
+FilterArgs make_filter(const smart_ctx *c);
+smart_status ensure_filter_table(smart_ctx *c);
+smart_status common_args(smart_ctx *c, const smart_maps *out, MapArgs &a);
+
+}  // namespace smart

@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t *
 // ------------------------------------------------------------- scan
 // exclusive scan of uint32/int32 counts (totals < 2^31), reduce-then-scan
 template <typename T>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict__ in, int32_t *__restrict__ out,
-                                                           int64_t n, int32_t *__restrict__ sums) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict__ in, int64_t n_in,
+                                                           int32_t *__restrict__ out, int64_t n,
+                                                           int32_t *__restrict__ sums) {
     __shared__ int32_t ws[SCAN_THREADS / 32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int32_t v[SCAN_ITEMS];
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict_
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         const int64_t i = base + k;
-        v[k] = i < n ? (int32_t)in[i] : 0;
+        v[k] = i < n_in ? (int32_t)in[i] : 0;
         acc += v[k];
     }
     // inclusive scan of per-thread totals across the block
@@ -176,19 +177,20 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t n, const int32_t *
 }
 
 template <typename T>
-static smart_status scan_impl(smart_ctx *ctx, const T *in, int32_t *out, int64_t n, int32_t *tmp, int64_t tmp_cap) {
+static smart_status scan_impl(smart_ctx *ctx, const T *in, int64_t n_in, int32_t *out, int64_t n, int32_t *tmp,
+                              int64_t tmp_cap) {
     if (n <= 0) return SMART_OK;
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 1) {
-        k_scan_tile<T><<<1, SCAN_THREADS, 0, ctx->stream>>>(in, out, n, nullptr);
+        k_scan_tile<T><<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n_in, out, n, nullptr);
         return check_cuda(ctx, cudaGetLastError(), "scan");
     }
     if (nb + 1 > tmp_cap) return fail(ctx, SMART_E_INTERNAL, "scan scratch too small");
     int32_t *sums = tmp;
-    k_scan_tile<T><<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, out, n, sums);
+    k_scan_tile<T><<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n_in, out, n, sums);
     smart_status st = check_cuda(ctx, cudaGetLastError(), "scan tiles");
     if (st != SMART_OK) return st;
-    st = scan_impl<int32_t>(ctx, sums, sums, nb, tmp + nb, tmp_cap - nb);
+    st = scan_impl<int32_t>(ctx, sums, nb, sums, nb, tmp + nb, tmp_cap - nb);
     if (st != SMART_OK) return st;
     k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(out, n, sums);
     return check_cuda(ctx, cudaGetLastError(), "scan add");
@@ -301,10 +303,10 @@ static unsigned grid_for(int64_t n, int threads) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 148 * 32));
 }
 
-smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out, int64_t n) {
-    smart_status st = ensure_alloc(ctx, (void **)&ctx->scan_tmp, ctx->cap_scan, scan_scratch(n), sizeof(int64_t), "scan scratch");
+smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out, int64_t n_in, int64_t n_out) {
+    smart_status st = ensure_alloc(ctx, (void **)&ctx->scan_tmp, ctx->cap_scan, scan_scratch(n_out), sizeof(int64_t), "scan scratch");
     if (st != SMART_OK) return st;
-    return scan_impl<int32_t>(ctx, in, out, n, (int32_t *)ctx->scan_tmp, ctx->cap_scan * 2);
+    return scan_impl<int32_t>(ctx, in, n_in, out, n_out, (int32_t *)ctx->scan_tmp, ctx->cap_scan * 2);
 }
 
 }  // namespace smart
@@ -348,7 +350,8 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
         uint32_t *ki = c->keys, *ko = c->keys_alt, *vi = c->vals, *vo = c->vals_alt;
         for (int shift = 0; shift < bits; shift += RADIX_BITS) {
             k_radix_hist<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, n, shift, ntiles, c->hist);
-            st = scan_impl<uint32_t>(c, c->hist, hscan, (int64_t)RADIX * ntiles, (int32_t *)c->scan_tmp, c->cap_scan * 2);
+            st = scan_impl<uint32_t>(c, c->hist, (int64_t)RADIX * ntiles, hscan, (int64_t)RADIX * ntiles,
+                                     (int32_t *)c->scan_tmp, c->cap_scan * 2);
             if (st != SMART_OK) return st;
             k_radix_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles, (const uint32_t *)hscan);
             if ((st = check_cuda(c, cudaGetLastError(), "k_radix_scatter")) != SMART_OK) return st;
@@ -368,7 +371,7 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
         if ((st = check_cuda(c, cudaGetLastError(), "k_run_counts")) != SMART_OK) return st;
     }
     // offsets[0..npix] = exclusive scan of counts[0..npix] (counts[npix] = 0)
-    st = scan_impl<int32_t>(c, counts, c->offsets, npix + 1, (int32_t *)c->scan_tmp, c->cap_scan * 2);
+    st = scan_impl<int32_t>(c, counts, npix + 1, c->offsets, npix + 1, (int32_t *)c->scan_tmp, c->cap_scan * 2);
     if (st != SMART_OK) return st;
     if (n > 0) {
         k_records<<<grid_for(n, 256), 256, 0, s>>>(N, c->keys, c->vals, n, ra, dec, e1, e2, w, c->ring_lat,

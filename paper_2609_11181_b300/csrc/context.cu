@@ -63,7 +63,12 @@ extern "C" smart_status smart_create(int nside_out, const smart_filter *filter, 
     c->T = smart_chord2(theta_ap_arcmin);
     c->area = 2.0 * SMART_PI * (0.5 * c->T);     // 2 pi (1 - cos theta_ap) = pi T
     c->stream = (cudaStream_t)cuda_stream;
-    if (cudaMalloc(&c->d_fp64_count, sizeof(unsigned long long)) != cudaSuccess) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        c->num_sms = sms;
+    if (cudaMalloc(&c->d_fp64_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_work, sizeof(int)) != cudaSuccess) {
+        if (c->d_fp64_count) cudaFree(c->d_fp64_count);
         delete c;
         return SMART_E_NOMEM;
     }
@@ -77,7 +82,7 @@ extern "C" void smart_destroy(smart_ctx *c) {
     void *bufs[] = {c->targets, c->rp_pix, c->rp_gal, c->rp_pix_cnt, c->rp_gal_cnt, c->own_binned,
                     c->own_np, c->keys, c->keys_alt, c->vals, c->vals_alt, c->offsets, c->rec_geo,
                     c->rec_shear, c->rec_radec, c->hist, c->hist_scan, c->scan_tmp, c->ring_lat, c->d_invalid,
-                    c->d_fp64_count};
+                    c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->d_fp64_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -115,6 +120,7 @@ extern "C" smart_status smart_set_targets(smart_ctx *c, const int64_t *pix, int6
     smart_status st = ensure_alloc(c, (void **)&c->targets, c->cap_targets, n, sizeof(int64_t), "targets");
     if (st != SMART_OK) return st;
     c->n_targets = n;
+    c->n_tiles = 0;
     if (n == 0) return SMART_OK;
     st = check_cuda(c, cudaMemcpyAsync(c->targets, pix, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream),
                     "copy targets");
@@ -132,9 +138,10 @@ extern "C" smart_status smart_set_targets(smart_ctx *c, const int64_t *pix, int6
     if (st != SMART_OK) return st;
     if (hb) {
         c->n_targets = 0;
+        c->n_tiles = 0;
         return fail(c, SMART_E_ARG, "smart_set_targets: pixels must be unique, ascending and in [0, 12 nside_out^2)");
     }
-    return SMART_OK;
+    return build_tiles(c);
 }
 
 extern "C" smart_status smart_set_binned(smart_ctx *c, const float *G1, const float *G2, const float *W,

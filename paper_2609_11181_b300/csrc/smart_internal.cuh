@@ -311,6 +311,17 @@ struct smart_ctx {
     int64_t *scan_tmp = nullptr;
     int64_t cap_scan = 0;
 
+    // pixel-mode launch state
+    int64_t *tiles = nullptr;                        // first target of each tile (+ end)
+    int64_t cap_tiles = 0, n_tiles = 0;
+    int32_t *tile_flag = nullptr;
+    int64_t cap_tile_flag = 0;
+    float4 *qtab = nullptr;                          // filter table (Schirmer)
+    int32_t *np_prefix = nullptr;                    // prefix of per-pixel counts (smart_set_binned input)
+    int64_t cap_np_prefix = 0;
+    int *d_work = nullptr;                           // tile counter of persistent launches
+    int num_sms = 148;
+
     // diagnostics
     unsigned long long *d_fp64_count = nullptr;
 };
@@ -326,6 +337,10 @@ smart_status build_ring_pairs(smart_ctx *ctx, double theta_disc, RingPair **out,
 double max_pixrad(int nside);
 
 // binning.cu
-smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
+// out[0..n_out) = exclusive prefix sums of in[0..n_in), inputs past n_in read as 0
+smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out, int64_t n_in, int64_t n_out);
+
+// aperture_pixel.cu
+smart_status build_tiles(smart_ctx *ctx);
 
 }  // namespace smart
