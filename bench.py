@@ -179,10 +179,20 @@ def cpu_baseline_pixel(wl, budget_s=15.0, seed=0):
                       f"{dt:.1f} s"}, pairs, dt, m
 
 
+PIXEL_WORKLOADS = {
+    # the headline configuration
+    "pixel4096": dict(nside=4096, area_deg2=15000.0, theta_ap=10.0, filt="schirmer"),
+    # a small case of the same kernels for profiling: 3,000 deg^2 cap at dec 60
+    # (polar and equatorial rings), NSIDE 2048, theta_ap = 20' (about as many
+    # pixels per aperture as NSIDE 4096 at 10'); 1 GB of full-sky arrays
+    "pixel2048": dict(nside=2048, area_deg2=3000.0, theta_ap=20.0, filt="schirmer", dec0=60.0),
+}
+
+
 def run_native_pixel(args, world, rank):
     dev = torch.device("cuda", torch.cuda.current_device())
     t_gen = time.perf_counter()
-    wl = workloads.pixel_workload(dev, api.pix2vec)
+    wl = workloads.pixel_workload(dev, api.pix2vec, **PIXEL_WORKLOADS[args.workload])
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     ctx = api.Context(wl.nside, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside)
@@ -260,9 +270,10 @@ def run_native_pixel(args, world, rank):
         "metric": METRIC, "value": round(value, 3), "unit": "Gpair/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "pixel4096", "desc": wl.desc, "targets": n, "pairs_per_step": pairs_step,
+        "config": {"workload": args.workload, "desc": wl.desc, "targets": n, "pairs_per_step": pairs_step,
                    "nside": wl.nside, "theta_ap_arcmin": wl.theta_ap_arcmin, "filter": wl.filter,
-                   "l2": "inputs (4.0 GB full-sky binned arrays) larger than L2; no flush",
+                   "l2": f"inputs ({sum(x.numel() * x.element_size() for x in inputs) / 1e9:.1f} GB full-sky binned "
+                         "arrays) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "map_time_ms": round(ms_step, 3),
         "kernel_ms_mean": round(kmean, 3),
@@ -292,7 +303,7 @@ def run_reference(args, world, rank):
     def oracle_centres(nside, p):
         return torch.from_numpy(oracle.pix2vec(nside, p.cpu().numpy())).to(p.device)
 
-    wl = workloads.pixel_workload(dev, oracle_centres)
+    wl = workloads.pixel_workload(dev, oracle_centres, **PIXEL_WORKLOADS[args.workload])
     times, vals = [], []
     cb = None
     for k in range(args.warmup + args.steps):
@@ -316,7 +327,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="pixel4096", choices=["pixel4096"])
+    ap.add_argument("--workload", default="pixel4096", choices=sorted(PIXEL_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -46,6 +46,11 @@ struct MapArgs {
     // tiles of targets (pixel mode): first target of each tile, n_tiles + 1 entries
     const int64_t *tiles;
     int64_t n_tiles;
+    const ToeInfo *toe;      // Toeplitz info per ring pair (pixel mode)
+    const float4 *toe_geo;   // per-offset (a, b, -b, c) of the Toeplitz ring pairs
+    const unsigned char *toe_ring;  // 1: every ring pair of this output ring is Toeplitz
+    const int32_t *gen_list;        // targets of the other rings (general kernel)
+    int64_t n_gen;
     int *work;               // tile counter of the persistent launch
     // brute-force inputs
     const int32_t *offsets;
@@ -87,7 +92,7 @@ __device__ __forceinline__ float filter_Q(const FilterArgs &f, const float4 *tab
         const float X2 = d2 * f.inv_ap2;
         return f.qnorm * X2 * (1.0f - X2);
     } else {
-        const float x = sqrtf(d2) * f.inv_ap;
+        const float x = d2 > 0.f ? d2 * rsqrtf(d2) * f.inv_ap : 0.f;
         return f.qnorm * qtab_eval(tab, x);
     }
 }
@@ -106,9 +111,25 @@ __device__ __forceinline__ void sin_hav_small(float u, float &sinu, float &h) {
     h = u2 * fmaf(u2, fmaf(u2, fmaf(u2, -1.0f / 80640.0f, 1.0f / 1440.0f), -1.0f / 48.0f), 0.25f);
 }
 
+// |u| <= pi: sine and cosine of v = u/2 in [-pi/2, pi/2] from their
+// Maclaurin series (to v^15 and v^16; truncation below 1e-10)
 __device__ __forceinline__ void sin_hav_wide(float u, float &sinu, float &h) {
-    float sh, ch;
-    sincosf(0.5f * u, &sh, &ch);
+    const float v = 0.5f * u, v2 = v * v;
+    float ps = fmaf(v2, -1.0f / 1307674368000.0f, 1.0f / 6227020800.0f);
+    ps = fmaf(v2, ps, -1.0f / 39916800.0f);
+    ps = fmaf(v2, ps, 1.0f / 362880.0f);
+    ps = fmaf(v2, ps, -1.0f / 5040.0f);
+    ps = fmaf(v2, ps, 1.0f / 120.0f);
+    ps = fmaf(v2, ps, -1.0f / 6.0f);
+    const float sh = fmaf(v * v2, ps, v);
+    float pc = fmaf(v2, 1.0f / 20922789888000.0f, -1.0f / 87178291200.0f);
+    pc = fmaf(v2, pc, 1.0f / 479001600.0f);
+    pc = fmaf(v2, pc, -1.0f / 3628800.0f);
+    pc = fmaf(v2, pc, 1.0f / 40320.0f);
+    pc = fmaf(v2, pc, -1.0f / 720.0f);
+    pc = fmaf(v2, pc, 1.0f / 24.0f);
+    pc = fmaf(v2, pc, -0.5f);
+    const float ch = fmaf(v2, pc, 1.0f);
     sinu = 2.0f * sh * ch;
     h = sh * sh;
 }

@@ -43,16 +43,57 @@ __device__ __forceinline__ int tpos(int m) { return (m & ~31) | ((m & 3) << 3) |
 __device__ __forceinline__ int qbase(int Q) { return Q + 3 * (Q & ~7); }   // tpos(4Q)
 
 // the float64 membership decision for a pair inside the guard band
-__device__ __noinline__ bool exact_member(const MapArgs &a, int64_t target_pix, int64_t bin_pix) {
+__device__ __noinline__ bool exact_member_pix(int64_t N0, int64_t N1, double T, unsigned long long *counter,
+                                              int64_t target_pix, int64_t bin_pix) {
     double x0, y0, z0, x1, y1, z1;
-    pix2vec64(a.N0, target_pix, x0, y0, z0);
-    pix2vec64(a.N1, bin_pix, x1, y1, z1);
-    atomicAdd(a.fp64_count, 1ull);
-    return member64(x0, y0, z0, x1, y1, z1, a.T);
+    pix2vec64(N0, target_pix, x0, y0, z0);
+    pix2vec64(N1, bin_pix, x1, y1, z1);
+    atomicAdd(counter, 1ull);
+    return member64(x0, y0, z0, x1, y1, z1, T);
 }
 
-// pixel-mode general pair loop for one target and one ring pair
-template <int KIND>
+__device__ __forceinline__ bool exact_member(const MapArgs &a, int64_t target_pix, int64_t bin_pix) {
+    return exact_member_pix(a.N0, a.N1, a.T, a.fp64_count, target_pix, bin_pix);
+}
+
+template <int MODE>
+__device__ __forceinline__ void sin_hav(float u, float &sinu, float &h) {
+    if (MODE == 0) sin_hav_narrow(u, sinu, h);
+    else if (MODE == 1) sin_hav_small(u, sinu, h);
+    else sin_hav_wide(u, sinu, h);
+}
+
+// one member pair's contribution (pixel mode)
+template <int KIND, int MODE>
+__device__ __forceinline__ void pixel_pair(const MapArgs &a, const RingPair &R, const float4 *qtab, float u, int p,
+                                           float &pe, float &pb, float &pv, float &pw, int &nn, int &nm) {
+    float sinu, h;
+    sin_hav<MODE>(u, sinu, h);
+    const float s2 = fmaf(R.B, h, R.A);
+    const float x = R.mrho0 * sinu;
+    const float y = fmaf(R.D, h, R.C);
+    const float xx = x * x;
+    const float sd2 = fmaf(y, y, xx);
+    const float cc = fmaf(y, y, -xx);
+    const float ss = -2.0f * x * y;
+    const float Q = filter_Q<KIND>(a.f, qtab, s2);
+    const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
+    const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
+    pe = fmaf(w, fmaf(g1, cc, g2 * ss), pe);
+    pb = fmaf(w, fmaf(g2, cc, -g1 * ss), pb);
+    pv = fmaf(Q * Q, __ldg(a.S2 + p), pv);
+    pw += __ldg(a.W + p);
+    nn += __ldg(a.NP + p);
+    nm += 1;
+}
+
+// pixel-mode general pair loop for one target and one ring pair; MODE picks
+// the sine series by the largest |u| of the ring pair (0: <= 0.05 rad,
+// 1: <= 0.45 rad, 2: |u| <= pi).  Pairs inside the float32 guard band are
+// set aside (a ring segment crosses the band edge at most twice) and
+// decided in float64 after the loop, which keeps the float64 code out of
+// the hot loop.
+template <int KIND, int MODE>
 __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
                                                 int64_t pix, const float4 *qtab, float &pe, float &pb, float &pv,
                                                 float &pw, int &nn, int &nm) {
@@ -63,39 +104,71 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
     const float fr = ((R.flags & RP_SHIFTED) ? 0.5f : 0.0f) - Xf;
     int kl, kh;
     window(R, fr, kl, kh);
-    int kk = (Xi + kl) % R.nr;
-    if (kk < 0) kk += R.nr;
-    const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
+    int kk0 = (Xi + kl) % R.nr;
+    if (kk0 < 0) kk0 += R.nr;
     const float u0 = fr * R.dphi;
-    float kf = (float)kl;
-    for (int k = kl; k <= kh; ++k) {
-        const float u = fmaf(kf, R.dphi, u0);
-        kf += 1.0f;
-        float sinu, h;
-        if (mode == 0) sin_hav_narrow(u, sinu, h);
-        else if (mode == 1) sin_hav_small(u, sinu, h);
-        else sin_hav_wide(u, sinu, h);
-        const float s2 = fmaf(R.B, h, R.A);
-        const int p = R.start + kk;
-        kk = (kk + 1 == R.nr) ? 0 : kk + 1;
-        if (s2 > a.Thi) continue;
-        if (s2 >= a.Tlo && !exact_member(a, pix, p)) continue;
-        const float x = R.mrho0 * sinu;
-        const float y = fmaf(R.D, h, R.C);
-        const float xx = x * x;
-        const float sd2 = fmaf(y, y, xx);
-        const float cc = fmaf(y, y, -xx);
-        const float ss = -2.0f * x * y;
-        const float Q = filter_Q<KIND>(a.f, qtab, s2);
-        const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
-        const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
-        pe = fmaf(w, fmaf(g1, cc, g2 * ss), pe);
-        pb = fmaf(w, fmaf(g2, cc, -g1 * ss), pb);
-        pv = fmaf(Q * Q, __ldg(a.S2 + p), pv);
-        pw += __ldg(a.W + p);
-        nn += __ldg(a.NP + p);
-        nm += 1;
+    int def0 = -1, def1 = -1, ndef = 0;
+    float ud0 = 0.f, ud1 = 0.f;
+    {
+        int kk = kk0;
+        float kf = (float)kl;
+#pragma unroll 1
+        for (int k = kl; k <= kh; ++k) {
+            const float u = fmaf(kf, R.dphi, u0);
+            kf += 1.0f;
+            float sinu, h;
+            sin_hav<MODE>(u, sinu, h);
+            const float s2 = fmaf(R.B, h, R.A);
+            const int p = R.start + kk;
+            kk = (kk + 1 == R.nr) ? 0 : kk + 1;
+            if (s2 > a.Thi) continue;
+            if (s2 >= a.Tlo) {
+                if (ndef == 0) {
+                    def0 = p;
+                    ud0 = u;
+                } else {
+                    def1 = p;
+                    ud1 = u;
+                }
+                ++ndef;
+                continue;
+            }
+            const float x = R.mrho0 * sinu;
+            const float y = fmaf(R.D, h, R.C);
+            const float xx = x * x;
+            const float sd2 = fmaf(y, y, xx);
+            const float cc = fmaf(y, y, -xx);
+            const float ss = -2.0f * x * y;
+            const float Q = filter_Q<KIND>(a.f, qtab, s2);
+            const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
+            const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
+            pe = fmaf(w, fmaf(g1, cc, g2 * ss), pe);
+            pb = fmaf(w, fmaf(g2, cc, -g1 * ss), pb);
+            pv = fmaf(Q * Q, __ldg(a.S2 + p), pv);
+            pw += __ldg(a.W + p);
+            nn += __ldg(a.NP + p);
+            nm += 1;
+        }
     }
+    if (ndef > 2) {
+        // cannot happen for HEALPix spacings; redo the guard-band pairs one by one
+        int kk = kk0;
+        float kf = (float)kl;
+        for (int k = kl; k <= kh; ++k) {
+            const float u = fmaf(kf, R.dphi, u0);
+            kf += 1.0f;
+            float sinu, h;
+            sin_hav<MODE>(u, sinu, h);
+            const float s2 = fmaf(R.B, h, R.A);
+            const int p = R.start + kk;
+            kk = (kk + 1 == R.nr) ? 0 : kk + 1;
+            if (s2 >= a.Tlo && s2 <= a.Thi && exact_member(a, pix, p))
+                pixel_pair<KIND, MODE>(a, R, qtab, u, p, pe, pb, pv, pw, nn, nm);
+        }
+        return;
+    }
+    if (ndef >= 1 && exact_member(a, pix, def0)) pixel_pair<KIND, MODE>(a, R, qtab, ud0, def0, pe, pb, pv, pw, nn, nm);
+    if (ndef >= 2 && exact_member(a, pix, def1)) pixel_pair<KIND, MODE>(a, R, qtab, ud1, def1, pe, pb, pv, pw, nn, nm);
 }
 
 // galaxies in the bin pixels [lo, lo + len) of a ring (indices mod nr)
@@ -107,21 +180,135 @@ __device__ __forceinline__ int ring_range_count(const int32_t *pre, int start, i
     return (__ldg(pre + start + nr) - __ldg(pre + start + lo)) + (__ldg(pre + start + hi - nr) - __ldg(pre + start));
 }
 
+// ------------------------------------------------------------------------
+// Toeplitz tables: for every ring pair whose bin ring has as many pixels as
+// the output ring (same nside), the pair geometry depends only on the index
+// offset delta.  One warp per ring pair evaluates geometry, filter and the
+// float32 membership class of every candidate offset once, for all tiles of
+// the output ring.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ bool toe_candidates(int64_t N0, int64_t N1, const RingPair &R, int nr0, int s0, int &dlo,
+                                               int &ncand, float &fr0) {
+    fr0 = ((R.flags & RP_SHIFTED) ? 0.5f : 0.0f) - 0.5f * (float)s0;
+    dlo = (int)ceilf(-fr0 - R.hw);
+    const int dhi = (int)floorf(-fr0 + R.hw);
+    ncand = dhi - dlo + 1;
+    return N0 == N1 && R.nr == nr0 && !(R.flags & RP_WIDE) && ncand >= 1 && ncand <= NCAND;
+}
+
+__device__ __forceinline__ void output_ring_shape(int64_t N0, int64_t i0, int &nr0, int &s0) {
+    if (i0 < N0) {
+        nr0 = (int)(4 * i0);
+        s0 = 1;
+    } else if (i0 <= 3 * N0) {
+        nr0 = (int)(4 * N0);
+        s0 = ((i0 - N0) & 1) == 0 ? 1 : 0;
+    } else {
+        nr0 = (int)(4 * (4 * N0 - i0));
+        s0 = 1;
+    }
+}
+
+__global__ void k_toe_count(const MapArgs a, int64_t nring, int32_t *__restrict__ cnt) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nring * a.kmax) return;
+    const int64_t i0 = 1 + idx / a.kmax;
+    const int e = (int)(idx % a.kmax);
+    int c = 0;
+    if (e < a.counts[i0 - 1]) {
+        int nr0, s0, dlo, ncand;
+        float fr0;
+        output_ring_shape(a.N0, i0, nr0, s0);
+        if (toe_candidates(a.N0, a.N1, a.table[idx], nr0, s0, dlo, ncand, fr0)) c = ncand;
+    }
+    cnt[idx] = c;
+}
+
 template <int KIND>
-__global__ void __launch_bounds__(NT, 4) k_map_pixel_tiled(const MapArgs a) {
+__global__ void k_toe_fill(const MapArgs a, int64_t nring, const int32_t *__restrict__ off,
+                           ToeInfo *__restrict__ info, float4 *__restrict__ pool) {
+    const int64_t idx = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (idx >= nring * a.kmax) return;
+    const int64_t i0 = 1 + idx / a.kmax;
+    const int e = (int)(idx % a.kmax);
+    ToeInfo ti;
+    ti.off = -1;
+    ti.dlo = ti.da = ti.L = ti.namb = 0;
+    ti.amb0 = ti.amb1 = ti.amb2 = 0;
+    int nr0, s0, dlo = 0, ncand = 0;
+    float fr0 = 0.f;
+    output_ring_shape(a.N0, i0, nr0, s0);
+    const bool ok = e < a.counts[i0 - 1] && toe_candidates(a.N0, a.N1, a.table[idx], nr0, s0, dlo, ncand, fr0);
+    if (ok) {
+        const RingPair R = a.table[idx];
+        const int base = off[idx];
+        const bool narrow = (R.hw + 1.0f) * R.dphi <= 0.05f;
+        int da = -1, db = -1, namb = 0, amb[3] = {0, 0, 0};
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            const int c = c0 + lane;
+            int k = 0;
+            float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < ncand) {
+                const float u = ((float)(dlo + c) + fr0) * R.dphi;
+                float sinu, h;
+                if (narrow) sin_hav_narrow(u, sinu, h);
+                else sin_hav_small(u, sinu, h);
+                const float s2 = fmaf(R.B, h, R.A);
+                k = s2 < a.Tlo ? 1 : (s2 > a.Thi ? 0 : 2);
+                if (k) {
+                    const float x = R.mrho0 * sinu;
+                    const float y = fmaf(R.D, h, R.C);
+                    const float xx = x * x;
+                    const float sd2 = fmaf(y, y, xx);
+                    const float Q = filter_Q<KIND>(a.f, a.f.qtab, s2);
+                    const float w = sd2 > 1e-30f ? Q / sd2 : 0.f;
+                    const float ga = w * fmaf(y, y, -xx);
+                    const float gb = w * (-2.0f * x * y);
+                    gv = make_float4(ga, gb, -gb, Q * Q);
+                }
+                pool[base + c] = gv;
+            }
+            const unsigned m1 = __ballot_sync(0xffffffffu, k == 1);
+            unsigned m2 = __ballot_sync(0xffffffffu, k == 2);
+            if (m1) {
+                if (da < 0) da = c0 + __ffs(m1) - 1;
+                db = c0 + 31 - __clz(m1);
+            }
+            while (m2) {
+                const int b = __ffs(m2) - 1;
+                m2 &= m2 - 1;
+                if (namb < 3) amb[namb] = c0 + b;
+                ++namb;
+            }
+        }
+        if (namb <= 3) {
+            ti.off = base;
+            ti.dlo = dlo;
+            ti.da = da < 0 ? 0 : da;
+            ti.L = da < 0 ? 0 : db - da + 1;
+            ti.namb = namb;
+            ti.amb0 = amb[0];
+            ti.amb1 = amb[1];
+            ti.amb2 = amb[2];
+        }
+    }
+    if (lane == 0) info[idx] = ti;
+}
+
+// ------------------------------------------------------------------------
+// Toeplitz kernel: output rings whose every ring pair is a Toeplitz pair.
+// Persistent CTAs take tiles of up to TS slots of one ring; thread tid owns
+// the slots 4 tid .. 4 tid + 3 and slides a window of staged pixels over
+// them.  Tiles of other rings are skipped (the general kernel has them).
+// ------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
     __shared__ float4 seg[SEGN];
-    __shared__ float4 geo[NCAND];                       // (a, b, -b, c) per candidate offset
-    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
     __shared__ int slot_t[TS];
-    __shared__ signed char cls[NCAND];
-    __shared__ int s_tile, s_da, s_db, s_namb, s_amb[8];
-    __shared__ float gpart[4][RB][NT];                  // general-path partial sums per slot
-    __shared__ int gcount[2][RB][NT];
+    __shared__ int s_tile;
 
     const int tid = threadIdx.x;
-    if (KIND != SMART_FILTER_POLY)
-        for (int i = tid; i < QTAB_BINS; i += NT) qtab[i] = a.f.qtab[i];
-
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(a.work, 1);
         __syncthreads();
@@ -129,6 +316,10 @@ __global__ void __launch_bounds__(NT, 4) k_map_pixel_tiled(const MapArgs a) {
         if (tile >= a.n_tiles) break;
         const int64_t tb = a.tiles[tile], te = a.tiles[tile + 1];
         const TargetRing tr0 = target_ring(a.N0, a.targets[tb]);
+        if (!a.toe_ring[tr0.i0 - 1]) {
+            __syncthreads();
+            continue;
+        }
         const int jbase = tr0.j0 & ~(TS - 1);
         const int nslots = min(TS, tr0.nr0 - jbase);
         const int64_t ring_start0 = a.targets[tb] - tr0.j0;
@@ -145,203 +336,192 @@ __global__ void __launch_bounds__(NT, 4) k_map_pixel_tiled(const MapArgs a) {
             tix[r] = (s0 + r < nslots) ? slot_t[s0 + r] : -1;
             any |= tix[r] >= 0;
         }
-        float SE[RB], cSE[RB], SB[RB], cSB[RB], SV[RB], cSV[RB], SW[RB], cSW[RB];
+        float SE[RB], cSE[RB], SB[RB], cSB[RB], SV[RB], SW[RB], cSW[RB];
         int NN[RB], NM[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-            SE[r] = cSE[r] = SB[r] = cSB[r] = SV[r] = cSV[r] = SW[r] = cSW[r] = 0.f;
+            SE[r] = cSE[r] = SB[r] = cSB[r] = SV[r] = SW[r] = cSW[r] = 0.f;
             NN[r] = NM[r] = 0;
         }
 
-        const RingPair *row = a.table + (int64_t)(tr0.i0 - 1) * a.kmax;
+        const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
         const int nent = a.counts[tr0.i0 - 1];
         for (int e = 0; e < nent; ++e) {
-            const RingPair R = row[e];
-            const float off_bin = (R.flags & RP_SHIFTED) ? 0.5f : 0.0f;
-            const float fr0 = off_bin - 0.5f * (float)tr0.s0;
-            const int dlo = (int)ceilf(-fr0 - R.hw);
-            const int dhi = (int)floorf(-fr0 + R.hw);
-            const int ncand = dhi - dlo + 1;
-            const bool toe = (a.N0 == a.N1) && (R.nr == tr0.nr0) && !(R.flags & RP_WIDE) && ncand >= 1 &&
-                             ncand <= NCAND;
-            if (toe) {
-                // ---- geometry, filter and membership per offset delta
-                const bool narrow = (R.hw + 1.0f) * R.dphi <= 0.05f;
-                for (int c = tid; c < ncand; c += NT) {
-                    const float u = ((float)(dlo + c) + fr0) * R.dphi;
-                    float sinu, h;
-                    if (narrow) sin_hav_narrow(u, sinu, h);
-                    else sin_hav_small(u, sinu, h);
-                    const float s2 = fmaf(R.B, h, R.A);
-                    const signed char k = s2 < a.Tlo ? 1 : (s2 > a.Thi ? 0 : 2);
-                    cls[c] = k;
-                    float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (k) {
-                        const float x = R.mrho0 * sinu;
-                        const float y = fmaf(R.D, h, R.C);
-                        const float xx = x * x;
-                        const float sd2 = fmaf(y, y, xx);
-                        const float Q = filter_Q<KIND>(a.f, qtab, s2);
-                        const float w = sd2 > 1e-30f ? Q / sd2 : 0.f;
-                        const float ga = w * fmaf(y, y, -xx);
-                        const float gb = w * (-2.0f * x * y);
-                        gv = make_float4(ga, gb, -gb, Q * Q);
-                    }
-                    geo[c] = gv;
+            const int rstart = __ldg(&a.table[row0 + e].start);
+            const int rnr = __ldg(&a.table[row0 + e].nr);
+            const ToeInfo ti = a.toe[row0 + e];
+            const int L = ti.L;
+            if (L > 0) {
+                // ---- stage the bin-ring segment: m -> bin pixel jbase + dlo + da + m
+                const int nseg = min(SEGN, nslots + L + 3);
+                const int k0 = jbase + ti.dlo + ti.da;
+                for (int m = tid; m < nseg; m += NT) {
+                    int kk = (k0 + m) % rnr;
+                    if (kk < 0) kk += rnr;
+                    const int p = rstart + kk;
+                    seg[tpos(m)] = make_float4(__ldg(a.G1 + p), __ldg(a.G2 + p), __ldg(a.S2 + p), __ldg(a.W + p));
                 }
                 __syncthreads();
-                if (tid == 0) {
-                    int da = -1, db = -2, na = 0;
-                    for (int c = 0; c < ncand; ++c) {
-                        if (cls[c] == 1) {
-                            if (da < 0) da = c;
-                            db = c;
-                        } else if (cls[c] == 2 && na < 8) {
-                            s_amb[na++] = c;
-                        }
-                    }
-                    s_da = da;
-                    s_db = db;
-                    s_namb = na;
-                }
-                __syncthreads();
-                const int da = s_da, L = s_db - s_da + 1;
-                if (L > 0) {
-                    // ---- stage the bin-ring segment: m -> bin pixel jbase + dlo + da + m
-                    const int nseg = min(SEGN, nslots + L + 3);
-                    const int k0 = jbase + dlo + da;
-                    for (int m = tid; m < nseg; m += NT) {
-                        int kk = (k0 + m) % R.nr;
-                        if (kk < 0) kk += R.nr;
-                        const int p = R.start + kk;
-                        seg[tpos(m)] = make_float4(__ldg(a.G1 + p), __ldg(a.G2 + p), __ldg(a.S2 + p), __ldg(a.W + p));
-                    }
-                    __syncthreads();
-                    if (any) {
-                        float pe[RB], pb[RB], pv[RB], pw[RB];
+                if (any) {
+                    float pe[RB], pb[RB], pv[RB], pw[RB];
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
-                        const float4 *g = geo + da;
-                        // slot s0 + r uses staged pixel s0 + r + dd for dd in [0, L)
-                        float4 P0 = seg[tpos(s0)], P1 = seg[tpos(s0 + 1)], P2 = seg[tpos(s0 + 2)];
-                        const int L4 = L & ~3;
-                        for (int dd = 0; dd < L4; dd += 4) {
-                            // pixels s0 + dd + 3 .. s0 + dd + 6: quad tid + dd/4 (lane 3), quad + 1 (lanes 0..2)
-                            const int Q = tid + (dd >> 2);
-                            const int b0 = qbase(Q), b1 = qbase(Q + 1);
-                            const float4 P3 = seg[b0 + 24];
-                            const float4 P4 = seg[b1];
-                            const float4 P5 = seg[b1 + 8];
-                            const float4 P6 = seg[b1 + 16];
-                            const float4 *gg = g + dd;
+                    for (int r = 0; r < RB; ++r) pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
+                    const float4 *g = a.toe_geo + ti.off + ti.da;
+                    // slot s0 + r uses staged pixel s0 + r + dd for dd in [0, L)
+                    float4 P0 = seg[tpos(s0)], P1 = seg[tpos(s0 + 1)], P2 = seg[tpos(s0 + 2)];
+                    const int L4 = L & ~3;
 #define SMART_ACC(r, P, G)                        \
     pe[r] = fmaf(G.x, P.x, fmaf(G.y, P.y, pe[r])); \
     pb[r] = fmaf(G.x, P.y, fmaf(G.z, P.x, pb[r])); \
     pv[r] = fmaf(G.w, P.z, pv[r]);                 \
     pw[r] += P.w;
-                            {
-                                const float4 G = gg[0];
-                                SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
-                            }
-                            {
-                                const float4 G = gg[1];
-                                SMART_ACC(0, P1, G) SMART_ACC(1, P2, G) SMART_ACC(2, P3, G) SMART_ACC(3, P4, G)
-                            }
-                            {
-                                const float4 G = gg[2];
-                                SMART_ACC(0, P2, G) SMART_ACC(1, P3, G) SMART_ACC(2, P4, G) SMART_ACC(3, P5, G)
-                            }
-                            {
-                                const float4 G = gg[3];
-                                SMART_ACC(0, P3, G) SMART_ACC(1, P4, G) SMART_ACC(2, P5, G) SMART_ACC(3, P6, G)
-                            }
-                            P0 = P4;
-                            P1 = P5;
-                            P2 = P6;
-                        }
-                        for (int dd = L4; dd < L; ++dd) {
-                            const float4 P3 = seg[tpos(s0 + dd + 3)];
-                            const float4 G = g[dd];
+                    for (int dd = 0; dd < L4; dd += 4) {
+                        // pixels s0 + dd + 3 .. s0 + dd + 6: quad tid + dd/4 (lane 3), quad + 1 (lanes 0..2)
+                        const int Q = tid + (dd >> 2);
+                        const int b0 = qbase(Q), b1 = qbase(Q + 1);
+                        {
+                            const float4 P3 = seg[b0 + 24];
+                            const float4 G = __ldg(g + dd);
                             SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
+                            P0 = P3;
+                        }
+                        {
+                            const float4 P4 = seg[b1];
+                            const float4 G = __ldg(g + dd + 1);
+                            SMART_ACC(0, P1, G) SMART_ACC(1, P2, G) SMART_ACC(2, P0, G) SMART_ACC(3, P4, G)
+                            P1 = P4;
+                        }
+                        {
+                            const float4 P5 = seg[b1 + 8];
+                            const float4 G = __ldg(g + dd + 2);
+                            SMART_ACC(0, P2, G) SMART_ACC(1, P0, G) SMART_ACC(2, P1, G) SMART_ACC(3, P5, G)
+                            P2 = P5;
+                        }
+                        {
+                            const float4 P6 = seg[b1 + 16];
+                            const float4 G = __ldg(g + dd + 3);
+                            SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P6, G)
+                            // window for the next block: pixels s0 + dd + 4, + 5, + 6
                             P0 = P1;
                             P1 = P2;
-                            P2 = P3;
+                            P2 = P6;
                         }
+                    }
+                    for (int dd = L4; dd < L; ++dd) {
+                        const float4 P3 = seg[tpos(s0 + dd + 3)];
+                        const float4 G = __ldg(g + dd);
+                        SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
+                        P0 = P1;
+                        P1 = P2;
+                        P2 = P3;
+                    }
 #undef SMART_ACC
 #pragma unroll
-                        for (int r = 0; r < RB; ++r) {
-                            if (tix[r] < 0) continue;
-                            kahan_add(SE[r], cSE[r], pe[r]);
-                            kahan_add(SB[r], cSB[r], pb[r]);
-                            kahan_add(SV[r], cSV[r], pv[r]);
-                            kahan_add(SW[r], cSW[r], pw[r]);
-                            NM[r] += L;
-                            NN[r] += ring_range_count(a.NPRE, R.start, R.nr, jbase + s0 + r + dlo + da, L);
-                        }
+                    for (int r = 0; r < RB; ++r) {
+                        if (tix[r] < 0) continue;
+                        kahan_add(SE[r], cSE[r], pe[r]);
+                        kahan_add(SB[r], cSB[r], pb[r]);
+                        SV[r] += pv[r];
+                        kahan_add(SW[r], cSW[r], pw[r]);
+                        NM[r] += L;
+                        NN[r] += ring_range_count(a.NPRE, rstart, rnr, jbase + s0 + r + ti.dlo + ti.da, L);
                     }
-                }
-                // ---- guard-band offsets: decided per target in float64
-                const int namb = s_namb;
-                if (any && namb > 0) {
-                    for (int ia = 0; ia < namb; ++ia) {
-                        const int c = s_amb[ia];
-                        const float4 G = geo[c];
-#pragma unroll
-                        for (int r = 0; r < RB; ++r) {
-                            if (tix[r] < 0) continue;
-                            const int64_t pix = ring_start0 + jbase + s0 + r;
-                            int kk = (jbase + s0 + r + dlo + c) % R.nr;
-                            if (kk < 0) kk += R.nr;
-                            const int p = R.start + kk;
-                            if (!exact_member(a, pix, p)) continue;
-                            const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
-                            kahan_add(SE[r], cSE[r], fmaf(G.x, g1, G.y * g2));
-                            kahan_add(SB[r], cSB[r], fmaf(G.x, g2, G.z * g1));
-                            kahan_add(SV[r], cSV[r], G.w * __ldg(a.S2 + p));
-                            kahan_add(SW[r], cSW[r], __ldg(a.W + p));
-                            NN[r] += __ldg(a.NP + p);
-                            NM[r] += 1;
-                        }
-                    }
-                }
-                __syncthreads();   // shared tables are rewritten by the next ring pair
-            } else if (any) {
-                // ---- general path: each target on its own; partial sums go
-                // through shared memory so the slot loop needs no register indexing
-#pragma unroll 1
-                for (int r = 0; r < RB; ++r) {
-                    float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
-                    int nn = 0, nm = 0;
-                    const int s = s0 + r;
-                    if (s < nslots && slot_t[s] >= 0) {
-                        TargetRing tr = tr0;
-                        tr.j0 = jbase + s;
-                        general_segment<KIND>(a, R, tr, ring_start0 + tr.j0, qtab, pe, pb, pv, pw, nn, nm);
-                    }
-                    gpart[0][r][tid] = pe;
-                    gpart[1][r][tid] = pb;
-                    gpart[2][r][tid] = pv;
-                    gpart[3][r][tid] = pw;
-                    gcount[0][r][tid] = nn;
-                    gcount[1][r][tid] = nm;
-                }
-#pragma unroll
-                for (int r = 0; r < RB; ++r) {
-                    kahan_add(SE[r], cSE[r], gpart[0][r][tid]);
-                    kahan_add(SB[r], cSB[r], gpart[1][r][tid]);
-                    kahan_add(SV[r], cSV[r], gpart[2][r][tid]);
-                    kahan_add(SW[r], cSW[r], gpart[3][r][tid]);
-                    NN[r] += gcount[0][r][tid];
-                    NM[r] += gcount[1][r][tid];
                 }
             }
+            // ---- guard-band offsets: decided per target in float64
+            if (any && ti.namb > 0) {
+                for (int ia = 0; ia < ti.namb; ++ia) {
+                    const int c = ia == 0 ? ti.amb0 : (ia == 1 ? ti.amb1 : ti.amb2);
+                    const float4 G = __ldg(a.toe_geo + ti.off + c);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) {
+                        if (tix[r] < 0) continue;
+                        const int64_t pix = ring_start0 + jbase + s0 + r;
+                        int kk = (jbase + s0 + r + ti.dlo + c) % rnr;
+                        if (kk < 0) kk += rnr;
+                        const int p = rstart + kk;
+                        if (!exact_member(a, pix, p)) continue;
+                        const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
+                        kahan_add(SE[r], cSE[r], fmaf(G.x, g1, G.y * g2));
+                        kahan_add(SB[r], cSB[r], fmaf(G.x, g2, G.z * g1));
+                        SV[r] += G.w * __ldg(a.S2 + p);
+                        kahan_add(SW[r], cSW[r], __ldg(a.W + p));
+                        NN[r] += __ldg(a.NP + p);
+                        NM[r] += 1;
+                    }
+                }
+            }
+            if (L > 0) __syncthreads();   // the staged segment is rewritten by the next ring pair
         }
 #pragma unroll
         for (int r = 0; r < RB; ++r)
             if (tix[r] >= 0)
-                finalise(a, tb + tix[r], SE[r], cSE[r], SB[r], cSB[r], SV[r], cSV[r], SW[r], cSW[r], NN[r], NM[r]);
+                finalise(a, tb + tix[r], SE[r], cSE[r], SB[r], cSB[r], SV[r], 0.f, SW[r], cSW[r], NN[r], NM[r]);
         __syncthreads();   // slot map and s_tile are rewritten by the next tile
     }
+}
+
+// ------------------------------------------------------------------------
+// General kernel: one thread per target of the other rings; consecutive
+// threads hold consecutive targets, so bin pixels are read coalesced.
+// ------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(128, 6) k_pixel_general(const MapArgs a) {
+    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
+    if (KIND != SMART_FILTER_POLY) {
+        for (int i = threadIdx.x; i < QTAB_BINS; i += blockDim.x) qtab[i] = a.f.qtab[i];
+        __syncthreads();
+    }
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= a.n_gen) return;
+    const int64_t t = a.gen_list[idx];
+    const int64_t pix = a.targets[t];
+    const TargetRing tr = target_ring(a.N0, pix);
+    const int64_t row0 = (int64_t)(tr.i0 - 1) * a.kmax;
+    const int nent = a.counts[tr.i0 - 1];
+    float SE = 0.f, cSE = 0.f, SB = 0.f, cSB = 0.f, SV = 0.f, SW = 0.f, cSW = 0.f;
+    int NN = 0, NM = 0;
+    for (int e = 0; e < nent; ++e) {
+        const RingPair R = a.table[row0 + e];
+        const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
+        float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
+        int nn = 0, nm = 0;
+        if (mode == 0) general_segment<KIND, 0>(a, R, tr, pix, qtab, pe, pb, pv, pw, nn, nm);
+        else if (mode == 1) general_segment<KIND, 1>(a, R, tr, pix, qtab, pe, pb, pv, pw, nn, nm);
+        else general_segment<KIND, 2>(a, R, tr, pix, qtab, pe, pb, pv, pw, nn, nm);
+        kahan_add(SE, cSE, pe);
+        kahan_add(SB, cSB, pb);
+        SV += pv;
+        kahan_add(SW, cSW, pw);
+        NN += nn;
+        NM += nm;
+    }
+    finalise(a, t, SE, cSE, SB, cSB, SV, 0.f, SW, cSW, NN, NM);
+}
+
+// ------------------------------------------------------------------------
+// ring classes and the general kernel's target list (built once per
+// target set and table)
+// ------------------------------------------------------------------------
+__global__ void k_toe_rings(const MapArgs a, int64_t nring, unsigned char *__restrict__ toe_ring) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nring) return;
+    const int nent = a.counts[i];
+    bool all = nent > 0;
+    for (int e = 0; e < nent && all; ++e) all = a.toe[i * a.kmax + e].off >= 0;
+    toe_ring[i] = all ? 1 : 0;
+}
+
+__global__ void k_gen_flags(const int64_t *__restrict__ t, int64_t n, int64_t N0,
+                            const unsigned char *__restrict__ toe_ring, int32_t *__restrict__ flag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        flag[k] = toe_ring[pix_to_ring(N0, t[k]).ring - 1] ? 0 : 1;
+}
+
+__global__ void k_gen_scatter(const int32_t *__restrict__ flag, const int32_t *__restrict__ idx, int64_t n,
+                              int32_t *__restrict__ list) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (flag[k]) list[idx[k]] = (int32_t)k;
 }
 
 // ------------------------------------------------------------------------
@@ -436,6 +616,67 @@ smart_status ensure_filter_table(smart_ctx *c) {
     return check_cuda(c, cudaGetLastError(), "k_filter_table");
 }
 
+// Toeplitz tables for every ring pair of the pixel-mode table (once per context)
+static smart_status build_toeplitz(smart_ctx *c, const MapArgs &a) {
+    const int64_t nring = 4 * (int64_t)c->nside_out - 1;
+    const int64_t nidx = nring * a.kmax;
+    int32_t *cnt = nullptr, *off = nullptr;
+    if (cudaMalloc(&cnt, (size_t)(2 * nidx + 1) * sizeof(int32_t)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(toeplitz counts) failed");
+    off = cnt + nidx;
+    k_toe_count<<<(unsigned)((nidx + 255) / 256), 256, 0, c->stream>>>(a, nring, cnt);
+    smart_status st = exclusive_scan_i32(c, cnt, off, nidx, nidx + 1);
+    int32_t total = 0;
+    if (st == SMART_OK) {
+        cudaMemcpyAsync(&total, off + nidx, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        st = check_cuda(c, cudaStreamSynchronize(c->stream), "toeplitz table size");
+    }
+    if (st == SMART_OK && cudaMalloc(&c->toe_info, (size_t)nidx * sizeof(ToeInfo)) != cudaSuccess)
+        st = fail(c, SMART_E_NOMEM, "cudaMalloc(toeplitz info) failed");
+    if (st == SMART_OK && cudaMalloc(&c->toe_geo, (size_t)std::max<int32_t>(total, 1) * sizeof(float4)) != cudaSuccess)
+        st = fail(c, SMART_E_NOMEM, "cudaMalloc(toeplitz geometry) failed");
+    if (st == SMART_OK) {
+        const unsigned blocks = (unsigned)((nidx * 32 + 255) / 256);
+        if (c->filter_kind == SMART_FILTER_POLY) k_toe_fill<SMART_FILTER_POLY><<<blocks, 256, 0, c->stream>>>(a, nring, off, c->toe_info, c->toe_geo);
+        else k_toe_fill<SMART_FILTER_SCHIRMER><<<blocks, 256, 0, c->stream>>>(a, nring, off, c->toe_info, c->toe_geo);
+        st = check_cuda(c, cudaGetLastError(), "k_toe_fill");
+    }
+    if (st == SMART_OK) st = check_cuda(c, cudaStreamSynchronize(c->stream), "toeplitz build");
+    cudaFree(cnt);
+    return st;
+}
+
+// which output rings go to the Toeplitz kernel, and the list of targets for
+// the general kernel (once per target set)
+static smart_status build_ring_classes(smart_ctx *c, const MapArgs &a) {
+    const int64_t nring = 4 * (int64_t)c->nside_out - 1;
+    const int64_t n = c->n_targets;
+    smart_status st = SMART_OK;
+    if (!c->toe_ring && cudaMalloc(&c->toe_ring, (size_t)nring) != cudaSuccess)
+        return fail(c, SMART_E_NOMEM, "cudaMalloc(ring classes) failed");
+    k_toe_rings<<<(unsigned)((nring + 127) / 128), 128, 0, c->stream>>>(a, nring, c->toe_ring);
+    st = ensure_alloc(c, (void **)&c->tile_flag, c->cap_tile_flag, 2 * n + 1, sizeof(int32_t), "target flags");
+    if (st != SMART_OK) return st;
+    int32_t *flag = c->tile_flag, *idx = c->tile_flag + n;
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    k_gen_flags<<<blocks, 256, 0, c->stream>>>(c->targets, n, c->nside_out, c->toe_ring, flag);
+    st = exclusive_scan_i32(c, flag, idx, n, n);
+    if (st != SMART_OK) return st;
+    int32_t last[2] = {0, 0};
+    cudaMemcpyAsync(&last[0], idx + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&last[1], flag + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    st = check_cuda(c, cudaStreamSynchronize(c->stream), "general target count");
+    if (st != SMART_OK) return st;
+    const int64_t ng = (int64_t)last[0] + last[1];
+    st = ensure_alloc(c, (void **)&c->gen_list, c->cap_gen_list, ng, sizeof(int32_t), "general target list");
+    if (st != SMART_OK) return st;
+    k_gen_scatter<<<blocks, 256, 0, c->stream>>>(flag, idx, n, c->gen_list);
+    st = check_cuda(c, cudaGetLastError(), "general target list");
+    if (st != SMART_OK) return st;
+    c->n_gen = ng;
+    c->gen_version = c->targets_version;
+    return SMART_OK;
+}
+
 FilterArgs make_filter(const smart_ctx *c) {
     FilterArgs f;
     f.inv_ap = (float)(1.0 / c->theta_ap);
@@ -497,6 +738,12 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     a.table = c->rp_pix;
     a.counts = c->rp_pix_cnt;
     a.kmax = c->kmax_pix;
+    if (!c->toe_info) {
+        st = build_toeplitz(c, a);
+        if (st != SMART_OK) return st;
+    }
+    a.toe = c->toe_info;
+    a.toe_geo = c->toe_geo;
     a.G1 = c->G1;
     a.G2 = c->G2;
     a.W = c->W;
@@ -508,9 +755,25 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     cudaMemsetAsync(c->d_fp64_count, 0, sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(c->d_work, 0, sizeof(int), c->stream);
     if (a.n == 0) return SMART_OK;
-    const int per_sm = 6;
-    const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * per_sm);
-    if (c->filter_kind == SMART_FILTER_POLY) k_map_pixel_tiled<SMART_FILTER_POLY><<<grid, NT, 0, c->stream>>>(a);
-    else k_map_pixel_tiled<SMART_FILTER_SCHIRMER><<<grid, NT, 0, c->stream>>>(a);
-    return check_cuda(c, cudaGetLastError(), "k_map_pixel_tiled launch");
+    if (c->gen_version != c->targets_version) {
+        st = build_ring_classes(c, a);
+        if (st != SMART_OK) return st;
+    }
+    a.toe_ring = c->toe_ring;
+    a.gen_list = c->gen_list;
+    a.n_gen = c->n_gen;
+    if (c->n_gen < a.n) {
+        const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * 4);
+        if (c->filter_kind == SMART_FILTER_POLY) k_pixel_toeplitz<SMART_FILTER_POLY><<<grid, NT, 0, c->stream>>>(a);
+        else k_pixel_toeplitz<SMART_FILTER_SCHIRMER><<<grid, NT, 0, c->stream>>>(a);
+        st = check_cuda(c, cudaGetLastError(), "k_pixel_toeplitz launch");
+        if (st != SMART_OK) return st;
+    }
+    if (c->n_gen > 0) {
+        const unsigned grid = (unsigned)((c->n_gen + 127) / 128);
+        if (c->filter_kind == SMART_FILTER_POLY) k_pixel_general<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a);
+        else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a);
+        st = check_cuda(c, cudaGetLastError(), "k_pixel_general launch");
+    }
+    return st;
 }

@@ -82,7 +82,8 @@ extern "C" void smart_destroy(smart_ctx *c) {
     void *bufs[] = {c->targets, c->rp_pix, c->rp_gal, c->rp_pix_cnt, c->rp_gal_cnt, c->own_binned,
                     c->own_np, c->keys, c->keys_alt, c->vals, c->vals_alt, c->offsets, c->rec_geo,
                     c->rec_shear, c->rec_radec, c->hist, c->hist_scan, c->scan_tmp, c->ring_lat, c->d_invalid,
-                    c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->d_fp64_count};
+                    c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
+                    c->toe_ring, c->gen_list, c->d_fp64_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -120,6 +121,7 @@ extern "C" smart_status smart_set_targets(smart_ctx *c, const int64_t *pix, int6
     smart_status st = ensure_alloc(c, (void **)&c->targets, c->cap_targets, n, sizeof(int64_t), "targets");
     if (st != SMART_OK) return st;
     c->n_targets = n;
+    c->targets_version += 1;
     c->n_tiles = 0;
     if (n == 0) return SMART_OK;
     st = check_cuda(c, cudaMemcpyAsync(c->targets, pix, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream),

@@ -261,6 +261,14 @@ static_assert(sizeof(RingPair) == 64, "RingPair layout");
 
 enum { RP_SHIFTED = 1, RP_WIDE = 2, RP_WHOLE = 4 };
 
+// Per ring pair of the pixel-mode table: where its per-offset geometry sits
+// in the Toeplitz pool (off = -1: not a Toeplitz pair), the candidate
+// offsets [dlo, dlo + ncand), the run [da, da + L) of certain members
+// (relative to dlo) and up to three offsets inside the float32 guard band.
+struct ToeInfo {
+    int off, dlo, da, L, namb, amb0, amb1, amb2;
+};
+
 }  // namespace smart
 
 // ---------------------------------------------------------------------------
@@ -320,6 +328,12 @@ struct smart_ctx {
     int32_t *np_prefix = nullptr;                    // prefix of per-pixel counts (smart_set_binned input)
     int64_t cap_np_prefix = 0;
     int *d_work = nullptr;                           // tile counter of persistent launches
+    smart::ToeInfo *toe_info = nullptr;              // Toeplitz tables of the pixel-mode ring pairs
+    float4 *toe_geo = nullptr;
+    unsigned char *toe_ring = nullptr;               // per output ring: all ring pairs Toeplitz
+    int32_t *gen_list = nullptr;                     // targets handled by the general kernel
+    int64_t cap_gen_list = 0, n_gen = 0;
+    int64_t targets_version = 0, gen_version = -1;
     int num_sms = 148;
 
     // diagnostics
