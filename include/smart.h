@@ -126,12 +126,23 @@ smart_status smart_bin_galaxies(smart_ctx *ctx, const double *ra_deg,
 
 /*
  * Give per-pixel sums directly (full-sky RING arrays at nside_bin, 12
- * nside_bin^2 entries each, device pointers, caller-owned and not copied:
- * keep them alive until the map calls have synced).  Same meaning as the
- * sums of smart_bin_galaxies.  Pixel-based maps only.
+ * nside_bin^2 entries each, device pointers).  Same meaning as the sums of
+ * smart_bin_galaxies.  The arrays are copied (asynchronously, on the
+ * context's stream) into the library's packed layout; call again after
+ * changing them.  Pixel-based maps only.
  */
 smart_status smart_set_binned(smart_ctx *ctx, const float *G1, const float *G2,
                               const float *W, const float *S2, const int32_t *n_p);
+
+/*
+ * Same input in the library's native layout: px holds 4 floats per pixel
+ * (G1, G2, S2, W) -- note S2 before W -- for the 12 nside_bin^2 RING pixels
+ * (device pointer, 16-byte aligned), n_p the counts.  Both arrays are
+ * borrowed, not copied: they are read by every later map call, so keep them
+ * alive and unchanged until then.  smart_set_binned copies its arrays into
+ * this layout instead.
+ */
+smart_status smart_set_binned_packed(smart_ctx *ctx, const float *px, const int32_t *n_p);
 
 /*
  * Brute-force map at galaxy positions (Sect. 3.1 steps 1-5; neighbours

@@ -38,6 +38,7 @@ SIGNATURES = {
     "smart_set_targets": (_I32, [_VP, _VP, _I64]),
     "smart_bin_galaxies": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _I64]),
     "smart_set_binned": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "smart_set_binned_packed": (_I32, [_VP, _VP, _VP]),
     "smart_map_bruteforce": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
     "smart_map_pixel": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
     "smart_ang2pix": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP]),

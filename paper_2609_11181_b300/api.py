@@ -132,6 +132,16 @@ class Context:
             "smart_set_binned")
         self._keep = [G1, G2, W, S2, n_p]
 
+    def set_binned_packed(self, px, n_p):
+        """px: float32 tensor of shape (npix, 4) holding (G1, G2, S2, W) per pixel; borrowed."""
+        m = self.npix_bin
+        if px.dim() != 2 or px.shape[1] != 4:
+            raise ValueError("px must have shape (npix, 4)")
+        self._check(self._lib.smart_set_binned_packed(
+            self._h, _ptr(px, torch.float32, "px", 4 * m), _ptr(n_p, torch.int32, "n_p", m)),
+            "smart_set_binned_packed")
+        self._keep = [px, n_p]
+
     # -- maps
     def _out(self, out):
         if out is None:

@@ -19,14 +19,14 @@
 
 namespace smart {
 
-constexpr int QTAB_BINS = 1024;      // filter table: cubic pieces on x = d / theta_ap in [0, 1]
+constexpr int QTAB_BINS = 1024;      // filter table: cubic pieces on the chord s / s_ap in [0, 1]
 
 struct FilterArgs {
     float inv_ap;      // 1 / theta_ap
     float inv_ap2;     // 1 / theta_ap^2
-    float qnorm;       // poly: 6 / (pi theta_ap^2); table filters: 1 / theta_ap^2
-    float inv_xc;      // Schirmer 1 / xc
-    const float4 *qtab;  // QTAB_BINS cubic coefficients of q(x) (table filters)
+    float qnorm;       // poly: 6 / (pi theta_ap^2)
+    float tab_scale;   // QTAB_BINS / sqrt(T): chord -> table coordinate
+    const float4 *qtab;  // QTAB_BINS cubic pieces of Q as a function of the chord (table filters)
 };
 
 struct MapArgs {
@@ -39,8 +39,8 @@ struct MapArgs {
     float Tlo, Thi;          // guard band around T (float32)
     double T, area;
     FilterArgs f;
-    // pixel-mode inputs
-    const float *G1, *G2, *W, *S2;
+    // pixel-mode inputs: (G1, G2, S2, W) per pixel and the galaxy count
+    const float4 *PX;
     const int32_t *NP;
     const int32_t *NPRE;     // exclusive prefix of NP over RING order (npix + 1)
     // tiles of targets (pixel mode): first target of each tile, n_tiles + 1 entries
@@ -73,27 +73,25 @@ __device__ __forceinline__ float sep2_from_chord2(float s2) {
     return s2 * fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 3150.0f, 1.0f / 560.0f), 1.0f / 90.0f), 1.0f / 12.0f), 1.0f);
 }
 
-// q(x) from the cubic table: x in [0, 1], bins of width 1/QTAB_BINS
-__device__ __forceinline__ float qtab_eval(const float4 *tab, float x) {
-    const float f = x * (float)QTAB_BINS;
-    int i = (int)f;
-    i = min(max(i, 0), QTAB_BINS - 1);
+// Q from the cubic table, indexed by the chord s = sqrt(s2) (uniform bins of
+// s / s_ap; Q is smooth in s because the separation d(s) is)
+__device__ __forceinline__ float qtab_eval(const float4 *tab, float s2, float scale) {
+    const float f = s2 * rsqrtf(fmaxf(s2, 1e-30f)) * scale;
+    const int i = min((int)f, QTAB_BINS - 1);
     const float t = f - (float)i;
     const float4 c = tab[i];
     return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
 }
 
 // Q(d) from the chord^2.  Polynomial filter in closed form; the Schirmer
-// filter through its cubic table (tab points to a shared-memory copy).
+// filter through its cubic table (tab: a shared-memory or global copy).
 template <int KIND>
 __device__ __forceinline__ float filter_Q(const FilterArgs &f, const float4 *tab, float s2) {
-    const float d2 = sep2_from_chord2(s2);
     if (KIND == SMART_FILTER_POLY) {
-        const float X2 = d2 * f.inv_ap2;
+        const float X2 = sep2_from_chord2(s2) * f.inv_ap2;
         return f.qnorm * X2 * (1.0f - X2);
     } else {
-        const float x = d2 > 0.f ? d2 * rsqrtf(d2) * f.inv_ap : 0.f;
-        return f.qnorm * qtab_eval(tab, x);
+        return qtab_eval(tab, s2, f.tab_scale);
     }
 }
 

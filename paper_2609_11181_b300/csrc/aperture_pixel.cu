@@ -40,6 +40,7 @@ static_assert(TS == NT * RB, "tile = threads x slots per thread");
 // block of 32, so that lanes reading m = 4 l + c hit 8 distinct 16-byte
 // bank groups in every quarter warp
 __device__ __forceinline__ int tpos(int m) { return (m & ~31) | ((m & 3) << 3) | ((m >> 2) & 7); }
+__device__ __forceinline__ int tpos_inv(int q) { return (q & ~31) | ((q & 7) << 2) | ((q >> 3) & 3); }
 __device__ __forceinline__ int qbase(int Q) { return Q + 3 * (Q & ~7); }   // tpos(4Q)
 
 // the float64 membership decision for a pair inside the guard band
@@ -78,11 +79,11 @@ __device__ __forceinline__ void pixel_pair(const MapArgs &a, const RingPair &R, 
     const float ss = -2.0f * x * y;
     const float Q = filter_Q<KIND>(a.f, qtab, s2);
     const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
-    const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
-    pe = fmaf(w, fmaf(g1, cc, g2 * ss), pe);
-    pb = fmaf(w, fmaf(g2, cc, -g1 * ss), pb);
-    pv = fmaf(Q * Q, __ldg(a.S2 + p), pv);
-    pw += __ldg(a.W + p);
+    const float4 g = __ldg(a.PX + p);
+    pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
+    pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
+    pv = fmaf(Q * Q, g.z, pv);
+    pw += g.w;
     nn += __ldg(a.NP + p);
     nm += 1;
 }
@@ -109,18 +110,22 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
     const float u0 = fr * R.dphi;
     int def0 = -1, def1 = -1, ndef = 0;
     float ud0 = 0.f, ud1 = 0.f;
-    {
-        int kk = kk0;
-        float kf = (float)kl;
+    // the window's pixels are [kk0, nr) then [0, rest) when it wraps
+    const int len = kh - kl + 1;
+    const int n1 = min(len, R.nr - kk0);
 #pragma unroll 1
-        for (int k = kl; k <= kh; ++k) {
+    for (int part = 0; part < 2; ++part) {
+        const int cnt = part == 0 ? n1 : len - n1;
+        const int pbeg = part == 0 ? R.start + kk0 : R.start;
+        float kf = (float)(part == 0 ? kl : kl + n1);
+#pragma unroll 1
+        for (int i = 0; i < cnt; ++i) {
             const float u = fmaf(kf, R.dphi, u0);
             kf += 1.0f;
             float sinu, h;
             sin_hav<MODE>(u, sinu, h);
             const float s2 = fmaf(R.B, h, R.A);
-            const int p = R.start + kk;
-            kk = (kk + 1 == R.nr) ? 0 : kk + 1;
+            const int p = pbeg + i;
             if (s2 > a.Thi) continue;
             if (s2 >= a.Tlo) {
                 if (ndef == 0) {
@@ -141,11 +146,11 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             const float ss = -2.0f * x * y;
             const float Q = filter_Q<KIND>(a.f, qtab, s2);
             const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
-            const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
-            pe = fmaf(w, fmaf(g1, cc, g2 * ss), pe);
-            pb = fmaf(w, fmaf(g2, cc, -g1 * ss), pb);
-            pv = fmaf(Q * Q, __ldg(a.S2 + p), pv);
-            pw += __ldg(a.W + p);
+            const float4 g = __ldg(a.PX + p);
+            pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
+            pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
+            pv = fmaf(Q * Q, g.z, pv);
+            pw += g.w;
             nn += __ldg(a.NP + p);
             nm += 1;
         }
@@ -355,11 +360,14 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
                 // ---- stage the bin-ring segment: m -> bin pixel jbase + dlo + da + m
                 const int nseg = min(SEGN, nslots + L + 3);
                 const int k0 = jbase + ti.dlo + ti.da;
-                for (int m = tid; m < nseg; m += NT) {
+                // walk shared-memory positions in order (conflict-free stores)
+                const int nseg32 = (nseg + 31) & ~31;
+                for (int q = tid; q < nseg32; q += NT) {
+                    const int m = tpos_inv(q);
+                    if (m >= nseg) continue;
                     int kk = (k0 + m) % rnr;
                     if (kk < 0) kk += rnr;
-                    const int p = rstart + kk;
-                    seg[tpos(m)] = make_float4(__ldg(a.G1 + p), __ldg(a.G2 + p), __ldg(a.S2 + p), __ldg(a.W + p));
+                    seg[q] = __ldg(a.PX + rstart + kk);
                 }
                 __syncthreads();
                 if (any) {
@@ -441,11 +449,11 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
                         if (kk < 0) kk += rnr;
                         const int p = rstart + kk;
                         if (!exact_member(a, pix, p)) continue;
-                        const float g1 = __ldg(a.G1 + p), g2 = __ldg(a.G2 + p);
-                        kahan_add(SE[r], cSE[r], fmaf(G.x, g1, G.y * g2));
-                        kahan_add(SB[r], cSB[r], fmaf(G.x, g2, G.z * g1));
-                        SV[r] += G.w * __ldg(a.S2 + p);
-                        kahan_add(SW[r], cSW[r], __ldg(a.W + p));
+                        const float4 px = __ldg(a.PX + p);
+                        kahan_add(SE[r], cSE[r], fmaf(G.x, px.x, G.y * px.y));
+                        kahan_add(SB[r], cSB[r], fmaf(G.x, px.y, G.z * px.x));
+                        SV[r] += G.w * px.z;
+                        kahan_add(SW[r], cSW[r], px.w);
                         NN[r] += __ldg(a.NP + p);
                         NM[r] += 1;
                     }
@@ -573,8 +581,10 @@ smart_status build_tiles(smart_ctx *c) {
 }
 
 // ------------------------------------------------------------------------
-// Schirmer filter table: cubic Hermite pieces of q(x) on QTAB_BINS bins of
-// x in [0, 1], from float64 values and analytic derivatives
+// Schirmer filter table: cubic Hermite pieces of Q on QTAB_BINS uniform bins
+// of the chord s in [0, s_ap] (s_ap^2 = T), from float64 values and
+// analytic derivatives; d = 2 asin(s/2), x = d / theta_ap,
+// Q = q(x) / theta_ap^2
 // ------------------------------------------------------------------------
 __device__ double schirmer_q(double x, double xc, double *dq) {
     const double r = x / xc;
@@ -594,13 +604,25 @@ __device__ double schirmer_q(double x, double xc, double *dq) {
     return th * g;
 }
 
-__global__ void k_filter_table(double xc, float4 *__restrict__ tab) {
+// Q and dQ/ds at chord s
+__device__ double schirmer_Q_of_chord(double s, double xc, double theta_ap, double *dQ) {
+    const double half = 0.5 * s;
+    const double d = 2.0 * asin(half);
+    const double dd = 1.0 / sqrt(1.0 - half * half);          // d d / d s
+    double dq;
+    const double q = schirmer_q(d / theta_ap, xc, &dq);
+    const double n = 1.0 / (theta_ap * theta_ap);
+    *dQ = n * dq * dd / theta_ap;
+    return n * q;
+}
+
+__global__ void k_filter_table(double xc, double theta_ap, double sap, float4 *__restrict__ tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= QTAB_BINS) return;
-    const double h = 1.0 / QTAB_BINS;
+    const double h = sap / QTAB_BINS;
     double d0, d1;
-    const double q0 = schirmer_q(i * h, xc, &d0);
-    const double q1 = schirmer_q((i + 1) * h, xc, &d1);
+    const double q0 = schirmer_Q_of_chord(i * h, xc, theta_ap, &d0);
+    const double q1 = schirmer_Q_of_chord((i + 1) * h, xc, theta_ap, &d1);
     d0 *= h;
     d1 *= h;
     // Hermite cubic on t in [0, 1]: q0 + d0 t + c2 t^2 + c3 t^3
@@ -612,7 +634,7 @@ __global__ void k_filter_table(double xc, float4 *__restrict__ tab) {
 smart_status ensure_filter_table(smart_ctx *c) {
     if (c->filter_kind == SMART_FILTER_POLY || c->qtab) return SMART_OK;
     if (cudaMalloc(&c->qtab, QTAB_BINS * sizeof(float4)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(filter table) failed");
-    k_filter_table<<<(QTAB_BINS + 127) / 128, 128, 0, c->stream>>>(c->xc, c->qtab);
+    k_filter_table<<<(QTAB_BINS + 127) / 128, 128, 0, c->stream>>>(c->xc, c->theta_ap, sqrt(c->T), c->qtab);
     return check_cuda(c, cudaGetLastError(), "k_filter_table");
 }
 
@@ -681,9 +703,8 @@ FilterArgs make_filter(const smart_ctx *c) {
     FilterArgs f;
     f.inv_ap = (float)(1.0 / c->theta_ap);
     f.inv_ap2 = (float)(1.0 / (c->theta_ap * c->theta_ap));
-    f.qnorm = c->filter_kind == SMART_FILTER_POLY ? (float)(6.0 / SMART_PI / (c->theta_ap * c->theta_ap))
-                                                  : (float)(1.0 / (c->theta_ap * c->theta_ap));
-    f.inv_xc = (float)(1.0 / c->xc);
+    f.qnorm = (float)(6.0 / SMART_PI / (c->theta_ap * c->theta_ap));
+    f.tab_scale = (float)(QTAB_BINS / sqrt(c->T));
     f.qtab = c->qtab;
     return f;
 }
@@ -726,7 +747,7 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
         if (st != SMART_OK) return st;
     }
     const int64_t npix = npix_of(c->nside_bin);
-    if (c->NP == c->own_np && c->have_catalog) {
+    if (c->binned_from_catalog && c->have_catalog) {
         a.NPRE = c->offsets;                 // the catalogue offsets are the count prefix
     } else {
         st = ensure_alloc(c, (void **)&c->np_prefix, c->cap_np_prefix, npix + 1, sizeof(int32_t), "count prefix");
@@ -744,10 +765,7 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     }
     a.toe = c->toe_info;
     a.toe_geo = c->toe_geo;
-    a.G1 = c->G1;
-    a.G2 = c->G2;
-    a.W = c->W;
-    a.S2 = c->S2;
+    a.PX = c->PX;
     a.NP = c->NP;
     a.tiles = c->tiles;
     a.n_tiles = c->n_tiles;

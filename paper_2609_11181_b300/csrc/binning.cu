@@ -258,10 +258,10 @@ __global__ void k_records(int64_t N, const uint32_t *__restrict__ keys, const ui
     }
 }
 
-// per-pixel sums in sorted order (one thread per pixel)
+// per-pixel sums in sorted order (one thread per pixel), written as
+// (G1, G2, S2, W) float4 plus the count
 __global__ void k_pixel_sums(const int32_t *__restrict__ off, int64_t npix, const float4 *__restrict__ sh,
-                             float *__restrict__ G1, float *__restrict__ G2, float *__restrict__ W,
-                             float *__restrict__ S2, int32_t *__restrict__ np) {
+                             float4 *__restrict__ px, int32_t *__restrict__ np) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t a = off[p], b = off[p + 1];
         float g1 = 0.f, g2 = 0.f, ww = 0.f, s2 = 0.f;
@@ -272,10 +272,7 @@ __global__ void k_pixel_sums(const int32_t *__restrict__ off, int64_t npix, cons
             ww += v.z;
             s2 += v.w;
         }
-        G1[p] = g1;
-        G2[p] = g2;
-        W[p] = ww;
-        S2[p] = s2;
+        px[p] = make_float4(g1, g2, s2, ww);
         np[p] = b - a;
     }
 }
@@ -326,8 +323,7 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     if (st != SMART_OK) return st;
     if (!c->offsets) {
         if (cudaMalloc(&c->offsets, (size_t)(npix + 1) * sizeof(int32_t)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(offsets) failed");
-        if (cudaMalloc(&c->own_binned, (size_t)4 * npix * sizeof(float)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(binned) failed");
-        if (cudaMalloc(&c->own_np, (size_t)(npix + 1) * sizeof(int32_t)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(counts) failed");
+        if ((st = ensure_own_binned_map(c)) != SMART_OK) return st;
         if (cudaMalloc(&c->ring_lat, (size_t)(4 * N) * sizeof(double)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(ring lat) failed");
         if (cudaMalloc(&c->d_invalid, sizeof(int)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(flag) failed");
         k_ring_lat<<<(unsigned)((4 * N + 127) / 128), 128, 0, c->stream>>>(N, c->ring_lat);
@@ -378,16 +374,12 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
                                                    c->rec_geo, c->rec_shear, c->rec_radec);
         if ((st = check_cuda(c, cudaGetLastError(), "k_records")) != SMART_OK) return st;
     }
-    float *B = c->own_binned;
-    k_pixel_sums<<<grid_for(npix, 256), 256, 0, s>>>(c->offsets, npix, c->rec_shear, B, B + npix, B + 2 * npix,
-                                                     B + 3 * npix, c->own_np);
+    k_pixel_sums<<<grid_for(npix, 256), 256, 0, s>>>(c->offsets, npix, c->rec_shear, c->own_px, c->own_np);
     if ((st = check_cuda(c, cudaGetLastError(), "k_pixel_sums")) != SMART_OK) return st;
-    c->G1 = B;
-    c->G2 = B + npix;
-    c->W = B + 2 * npix;
-    c->S2 = B + 3 * npix;
+    c->PX = c->own_px;
     c->NP = c->own_np;
     c->have_binned = true;
+    c->binned_from_catalog = true;
     c->have_catalog = true;
     c->n_gal = n;
     int inv = 0;
@@ -425,16 +417,23 @@ extern "C" smart_status smart_get_catalog(smart_ctx *c, int64_t *perm, int64_t *
     return check_cuda(c, cudaGetLastError(), "smart_get_catalog");
 }
 
+__global__ void k_unpack(const float4 *__restrict__ px, const int32_t *__restrict__ np, int64_t npix,
+                         float *__restrict__ G1, float *__restrict__ G2, float *__restrict__ W, float *__restrict__ S2,
+                         int32_t *__restrict__ n) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = px[p];
+        if (G1) G1[p] = v.x;
+        if (G2) G2[p] = v.y;
+        if (S2) S2[p] = v.z;
+        if (W) W[p] = v.w;
+        if (n) n[p] = np[p];
+    }
+}
+
 extern "C" smart_status smart_get_binned(smart_ctx *c, float *G1, float *G2, float *W, float *S2, int32_t *n_p) {
     if (!c) return SMART_E_ARG;
     if (!c->have_binned) return fail(c, SMART_E_STATE, "smart_get_binned: no binned map");
-    const size_t npix = (size_t)npix_of(c->nside_bin);
-    const void *src[5] = {c->G1, c->G2, c->W, c->S2, c->NP};
-    void *dst[5] = {G1, G2, W, S2, n_p};
-    for (int k = 0; k < 5; ++k)
-        if (dst[k]) {
-            smart_status st = check_cuda(c, cudaMemcpyAsync(dst[k], src[k], npix * 4, cudaMemcpyDeviceToDevice, c->stream), "smart_get_binned");
-            if (st != SMART_OK) return st;
-        }
-    return SMART_OK;
+    const int64_t npix = npix_of(c->nside_bin);
+    k_unpack<<<grid_for(npix, 256), 256, 0, c->stream>>>(c->PX, c->NP, npix, G1, G2, W, S2, n_p);
+    return check_cuda(c, cudaGetLastError(), "smart_get_binned");
 }

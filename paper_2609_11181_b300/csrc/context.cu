@@ -2,6 +2,7 @@
 // context (the C ABI declared in include/smart.h).
 #include <math.h>
 
+#include <algorithm>
 #include <chrono>
 #include <thread>
 
@@ -79,7 +80,7 @@ extern "C" smart_status smart_create(int nside_out, const smart_filter *filter, 
 extern "C" void smart_destroy(smart_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    void *bufs[] = {c->targets, c->rp_pix, c->rp_gal, c->rp_pix_cnt, c->rp_gal_cnt, c->own_binned,
+    void *bufs[] = {c->targets, c->rp_pix, c->rp_gal, c->rp_pix_cnt, c->rp_gal_cnt, c->own_px,
                     c->own_np, c->keys, c->keys_alt, c->vals, c->vals_alt, c->offsets, c->rec_geo,
                     c->rec_shear, c->rec_radec, c->hist, c->hist_scan, c->scan_tmp, c->ring_lat, c->d_invalid,
                     c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
@@ -146,16 +147,54 @@ extern "C" smart_status smart_set_targets(smart_ctx *c, const int64_t *pix, int6
     return build_tiles(c);
 }
 
+__global__ void k_pack(const float *__restrict__ G1, const float *__restrict__ G2, const float *__restrict__ W,
+                       const float *__restrict__ S2, const int32_t *__restrict__ n_in, int64_t npix,
+                       float4 *__restrict__ px, int32_t *__restrict__ n_out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        px[p] = make_float4(G1[p], G2[p], S2[p], W[p]);
+        n_out[p] = n_in[p];
+    }
+}
+
+static smart_status ensure_own_binned(smart_ctx *c) {
+    const int64_t npix = npix_of(c->nside_bin);
+    if (!c->own_px && cudaMalloc(&c->own_px, (size_t)npix * sizeof(float4)) != cudaSuccess)
+        return fail(c, SMART_E_NOMEM, "cudaMalloc(binned map) failed");
+    if (!c->own_np && cudaMalloc(&c->own_np, (size_t)(npix + 1) * sizeof(int32_t)) != cudaSuccess)
+        return fail(c, SMART_E_NOMEM, "cudaMalloc(binned counts) failed");
+    return SMART_OK;
+}
+
+namespace smart {
+smart_status ensure_own_binned_map(smart_ctx *c) { return ensure_own_binned(c); }
+}
+
 extern "C" smart_status smart_set_binned(smart_ctx *c, const float *G1, const float *G2, const float *W,
                                          const float *S2, const int32_t *n_p) {
     if (!c) return SMART_E_ARG;
     if (!G1 || !G2 || !W || !S2 || !n_p) return fail(c, SMART_E_ARG, "smart_set_binned: null pointer");
-    c->G1 = G1;
-    c->G2 = G2;
-    c->W = W;
-    c->S2 = S2;
+    smart_status st = ensure_own_binned(c);
+    if (st != SMART_OK) return st;
+    const int64_t npix = npix_of(c->nside_bin);
+    const unsigned blocks = (unsigned)std::min<int64_t>((npix + 255) / 256, (int64_t)c->num_sms * 16);
+    k_pack<<<blocks, 256, 0, c->stream>>>(G1, G2, W, S2, n_p, npix, c->own_px, c->own_np);
+    st = check_cuda(c, cudaGetLastError(), "k_pack");
+    if (st != SMART_OK) return st;
+    c->PX = c->own_px;
+    c->NP = c->own_np;
+    c->have_binned = true;
+    c->binned_from_catalog = false;
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_set_binned_packed(smart_ctx *c, const float *px, const int32_t *n_p) {
+    if (!c) return SMART_E_ARG;
+    if (!px || !n_p) return fail(c, SMART_E_ARG, "smart_set_binned_packed: null pointer");
+    if (((uintptr_t)px & 15) != 0) return fail(c, SMART_E_ARG, "smart_set_binned_packed: map not 16-byte aligned");
+    c->PX = (const float4 *)px;
     c->NP = n_p;
     c->have_binned = true;
+    c->binned_from_catalog = false;
     return SMART_OK;
 }
 

@@ -294,12 +294,14 @@ struct smart_ctx {
     int *rp_pix_cnt = nullptr, *rp_gal_cnt = nullptr;
     int kmax_pix = 0, kmax_gal = 0;
 
-    // binned maps: either owned (from bin_galaxies) or borrowed (set_binned)
-    const float *G1 = nullptr, *G2 = nullptr, *W = nullptr, *S2 = nullptr;
+    // binned maps, one float4 (G1, G2, S2, W) per pixel plus an int32 count:
+    // owned (smart_bin_galaxies, smart_set_binned) or borrowed (smart_set_binned_packed)
+    const float4 *PX = nullptr;
     const int32_t *NP = nullptr;
-    float *own_binned = nullptr;     // 4 * npix floats
-    int32_t *own_np = nullptr;
+    float4 *own_px = nullptr;        // npix
+    int32_t *own_np = nullptr;       // npix + 1
     bool have_binned = false;
+    bool binned_from_catalog = false;   // the catalogue offsets are then the count prefix
 
     // sorted catalogue
     int64_t n_gal = 0, cap_gal = 0;
@@ -356,5 +358,8 @@ smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out,
 
 // aperture_pixel.cu
 smart_status build_tiles(smart_ctx *ctx);
+
+// context.cu
+smart_status ensure_own_binned_map(smart_ctx *ctx);
 
 }  // namespace smart
