@@ -169,10 +169,11 @@ __device__ __forceinline__ void lattice_position(const TargetRing &t, int q, int
         Xi = t.j0;
         Xf = 0.5f * (float)t.s0;
     } else {
-        const int64_t num = (int64_t)(2 * t.j0 + t.s0) * q;
-        const int64_t den = 2 * (int64_t)t.q0;
-        const int64_t qi = num / den;
-        Xi = (int)qi;
+        // num < 2^31 for nside <= 8192: (2 j0 + s0) <= 2^16, q <= 2^13
+        const int num = (2 * t.j0 + t.s0) * q;
+        const int den = 2 * t.q0;
+        const int qi = num / den;
+        Xi = qi;
         Xf = (float)(num - qi * den) / (float)den;
     }
 }
@@ -187,20 +188,23 @@ __device__ __forceinline__ void window(const RingPair &R, float fr, int &kl, int
     }
 }
 
+// summed normalisation (Sect. 2.4): nbar = SW / A, M = S / nbar,
+// sigma^2 = SV / (2 nbar^2).  The compensated weight sum is carried to
+// float64 (its reported value); the ratio A / SW is then applied in float32.
 __device__ __forceinline__ void finalise(const MapArgs &a, int64_t t, float se, float cse, float sb, float csb,
                                          float sv, float csv, float sw, float csw, int64_t cnt, int nmem) {
     const double SW = (double)sw - (double)csw;
-    double me = 0.0, mb = 0.0, vv = 0.0;
+    float me = 0.f, mb = 0.f, vv = 0.f;
     if (SW > 0.0) {
-        const double nbar = SW / a.area;
-        me = ((double)se - (double)cse) / nbar;
-        mb = ((double)sb - (double)csb) / nbar;
-        vv = ((double)sv - (double)csv) / (2.0 * nbar * nbar);
+        const float r = (float)a.area / (float)SW;       // 1 / nbar
+        me = (se - cse) * r;
+        mb = (sb - csb) * r;
+        vv = 0.5f * (sv - csv) * r * r;
     }
     if (a.sum_w) a.sum_w[t] = SW;
-    if (a.map_e) a.map_e[t] = (float)me;
-    if (a.map_b) a.map_b[t] = (float)mb;
-    if (a.var) a.var[t] = (float)vv;
+    if (a.map_e) a.map_e[t] = me;
+    if (a.map_b) a.map_b[t] = mb;
+    if (a.var) a.var[t] = vv;
     if (a.count) a.count[t] = cnt;
     if (a.members) a.members[t] = nmem;
 }

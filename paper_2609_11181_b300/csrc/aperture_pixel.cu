@@ -305,11 +305,75 @@ __global__ void k_toe_fill(const MapArgs a, int64_t nring, const int32_t *__rest
 // Toeplitz kernel: output rings whose every ring pair is a Toeplitz pair.
 // Persistent CTAs take tiles of up to TS slots of one ring; thread tid owns
 // the slots 4 tid .. 4 tid + 3 and slides a window of staged pixels over
-// them.  Tiles of other rings are skipped (the general kernel has them).
+// them.  Per ring pair the CTA stages, with cp.async into a double buffer,
+// the bin-ring segment the tile needs (16-byte pixels in the transposed
+// layout), the per-offset geometry of the ring pair and the prefix counts
+// of the segment; ring pair e + 1 is in flight while e is summed.  Tiles
+// of other rings are skipped (the general kernel has them).
 // ------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// floor(a / b) for -b <= a < 2b
+__device__ __forceinline__ int wraps(int a, int b) { return a < 0 ? -1 : (a >= b ? 1 : 0); }
+
+constexpr int PREN = SEGN + 8;
+constexpr int PREQ = PREN / 4;        // prefix counts in 4 planes: m -> (m & 3) * PREQ + (m >> 2)
+static_assert(PREN % 4 == 0, "prefix planes");
+
+__device__ __forceinline__ int ppos(int m) { return (m & 3) * PREQ + (m >> 2); }
+
+struct ToeStage {
+    int start, nr, k0, L, off;
+};
+
+// issue the copies of ring pair e of a tile into buffer b
+__device__ __forceinline__ ToeStage toe_stage(const MapArgs &a, int64_t row0, int e, int jbase, int nslots,
+                                              float4 (*seg)[SEGN], float4 (*geo)[NCAND], int (*pre)[PREN], int b,
+                                              int tid) {
+    ToeStage t;
+    t.start = __ldg(&a.table[row0 + e].start);
+    t.nr = __ldg(&a.table[row0 + e].nr);
+    const ToeInfo ti = a.toe[row0 + e];
+    t.L = ti.L;
+    t.off = ti.off;
+    t.k0 = jbase + ti.dlo + ti.da;
+    if (t.L > 0) {
+        const int nseg = min(SEGN, nslots + t.L + 3);
+        const int nseg32 = (nseg + 31) & ~31;
+        // -nr < k0 + m < 2 nr for every staged m (the window is shorter than the ring)
+        for (int q = tid; q < nseg32; q += NT) {        // shared-memory positions in order
+            const int m = tpos_inv(q);
+            if (m >= nseg) continue;
+            int kk = t.k0 + m;
+            kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
+            cp_async16(&seg[b][q], a.PX + t.start + kk);
+        }
+        for (int c = tid; c < t.L; c += NT) cp_async16(&geo[b][c], a.toe_geo + ti.off + ti.da + c);
+        const int npre = min(PREN, nslots + t.L + 1);
+        for (int m = tid; m < npre; m += NT) {
+            int kk = t.k0 + m;
+            kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
+            cp_async4(&pre[b][ppos(m)], a.NPRE + t.start + kk);
+        }
+    }
+    cp_async_commit();
+    return t;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
-    __shared__ float4 seg[SEGN];
+    __shared__ __align__(16) float4 seg[2][SEGN];
+    __shared__ __align__(16) float4 geo[2][NCAND];
+    __shared__ int pre[2][PREN];
     __shared__ int slot_t[TS];
     __shared__ int s_tile;
 
@@ -328,10 +392,14 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
         const int jbase = tr0.j0 & ~(TS - 1);
         const int nslots = min(TS, tr0.nr0 - jbase);
         const int64_t ring_start0 = a.targets[tb] - tr0.j0;
+        const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
+        const int nent = a.counts[tr0.i0 - 1];
         for (int s = tid; s < TS; s += NT) slot_t[s] = -1;
         __syncthreads();
         for (int64_t t = tb + tid; t < te; t += NT) slot_t[(int)(a.targets[t] - ring_start0) - jbase] = (int)(t - tb);
-        __syncthreads();
+
+        ToeStage cur = toe_stage(a, row0, 0, jbase, nslots, seg, geo, pre, 0, tid);
+        __syncthreads();      // slot map written
 
         const int s0 = RB * tid;
         int tix[RB];
@@ -349,95 +417,87 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
             NN[r] = NM[r] = 0;
         }
 
-        const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
-        const int nent = a.counts[tr0.i0 - 1];
         for (int e = 0; e < nent; ++e) {
-            const int rstart = __ldg(&a.table[row0 + e].start);
-            const int rnr = __ldg(&a.table[row0 + e].nr);
-            const ToeInfo ti = a.toe[row0 + e];
-            const int L = ti.L;
-            if (L > 0) {
-                // ---- stage the bin-ring segment: m -> bin pixel jbase + dlo + da + m
-                const int nseg = min(SEGN, nslots + L + 3);
-                const int k0 = jbase + ti.dlo + ti.da;
-                // walk shared-memory positions in order (conflict-free stores)
-                const int nseg32 = (nseg + 31) & ~31;
-                for (int q = tid; q < nseg32; q += NT) {
-                    const int m = tpos_inv(q);
-                    if (m >= nseg) continue;
-                    int kk = (k0 + m) % rnr;
-                    if (kk < 0) kk += rnr;
-                    seg[q] = __ldg(a.PX + rstart + kk);
-                }
-                __syncthreads();
-                if (any) {
-                    float pe[RB], pb[RB], pv[RB], pw[RB];
+            const int b = e & 1;
+            cp_async_wait_all();
+            __syncthreads();       // ring pair e staged; everyone is done with buffer b ^ 1
+            ToeStage nxt;
+            if (e + 1 < nent) nxt = toe_stage(a, row0, e + 1, jbase, nslots, seg, geo, pre, b ^ 1, tid);
+            const int L = cur.L;
+            if (L > 0 && any) {
+                float pe[RB], pb[RB], pv[RB], pw[RB];
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
-                    const float4 *g = a.toe_geo + ti.off + ti.da;
-                    // slot s0 + r uses staged pixel s0 + r + dd for dd in [0, L)
-                    float4 P0 = seg[tpos(s0)], P1 = seg[tpos(s0 + 1)], P2 = seg[tpos(s0 + 2)];
-                    const int L4 = L & ~3;
+                for (int r = 0; r < RB; ++r) pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
+                const float4 *g = geo[b];
+                const float4 *sg = seg[b];
+                // slot s0 + r uses staged pixel s0 + r + dd for dd in [0, L)
+                float4 P0 = sg[tpos(s0)], P1 = sg[tpos(s0 + 1)], P2 = sg[tpos(s0 + 2)];
+                const int L4 = L & ~3;
 #define SMART_ACC(r, P, G)                        \
     pe[r] = fmaf(G.x, P.x, fmaf(G.y, P.y, pe[r])); \
     pb[r] = fmaf(G.x, P.y, fmaf(G.z, P.x, pb[r])); \
     pv[r] = fmaf(G.w, P.z, pv[r]);                 \
     pw[r] += P.w;
-                    for (int dd = 0; dd < L4; dd += 4) {
-                        // pixels s0 + dd + 3 .. s0 + dd + 6: quad tid + dd/4 (lane 3), quad + 1 (lanes 0..2)
-                        const int Q = tid + (dd >> 2);
-                        const int b0 = qbase(Q), b1 = qbase(Q + 1);
-                        {
-                            const float4 P3 = seg[b0 + 24];
-                            const float4 G = __ldg(g + dd);
-                            SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
-                            P0 = P3;
-                        }
-                        {
-                            const float4 P4 = seg[b1];
-                            const float4 G = __ldg(g + dd + 1);
-                            SMART_ACC(0, P1, G) SMART_ACC(1, P2, G) SMART_ACC(2, P0, G) SMART_ACC(3, P4, G)
-                            P1 = P4;
-                        }
-                        {
-                            const float4 P5 = seg[b1 + 8];
-                            const float4 G = __ldg(g + dd + 2);
-                            SMART_ACC(0, P2, G) SMART_ACC(1, P0, G) SMART_ACC(2, P1, G) SMART_ACC(3, P5, G)
-                            P2 = P5;
-                        }
-                        {
-                            const float4 P6 = seg[b1 + 16];
-                            const float4 G = __ldg(g + dd + 3);
-                            SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P6, G)
-                            // window for the next block: pixels s0 + dd + 4, + 5, + 6
-                            P0 = P1;
-                            P1 = P2;
-                            P2 = P6;
-                        }
-                    }
-                    for (int dd = L4; dd < L; ++dd) {
-                        const float4 P3 = seg[tpos(s0 + dd + 3)];
-                        const float4 G = __ldg(g + dd);
+                for (int dd = 0; dd < L4; dd += 4) {
+                    // pixels s0 + dd + 3 .. s0 + dd + 6: quad tid + dd/4 (lane 3), quad + 1 (lanes 0..2)
+                    const int Q = tid + (dd >> 2);
+                    const int b0 = qbase(Q), b1 = qbase(Q + 1);
+                    {
+                        const float4 P3 = sg[b0 + 24];
+                        const float4 G = g[dd];
                         SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
+                        P0 = P3;
+                    }
+                    {
+                        const float4 P4 = sg[b1];
+                        const float4 G = g[dd + 1];
+                        SMART_ACC(0, P1, G) SMART_ACC(1, P2, G) SMART_ACC(2, P0, G) SMART_ACC(3, P4, G)
+                        P1 = P4;
+                    }
+                    {
+                        const float4 P5 = sg[b1 + 8];
+                        const float4 G = g[dd + 2];
+                        SMART_ACC(0, P2, G) SMART_ACC(1, P0, G) SMART_ACC(2, P1, G) SMART_ACC(3, P5, G)
+                        P2 = P5;
+                    }
+                    {
+                        const float4 P6 = sg[b1 + 16];
+                        const float4 G = g[dd + 3];
+                        SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P6, G)
+                        // window for the next block: pixels s0 + dd + 4, + 5, + 6
                         P0 = P1;
                         P1 = P2;
-                        P2 = P3;
+                        P2 = P6;
                     }
+                }
+                for (int dd = L4; dd < L; ++dd) {
+                    const float4 P3 = sg[tpos(s0 + dd + 3)];
+                    const float4 G = g[dd];
+                    SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
+                    P0 = P1;
+                    P1 = P2;
+                    P2 = P3;
+                }
 #undef SMART_ACC
+                // galaxies in [k0 + s, k0 + s + L) from the staged prefix, with the
+                // ring total added for every pass over the ring's end
+                const int ring_tot = __ldg(a.NPRE + cur.start + cur.nr) - __ldg(a.NPRE + cur.start);
 #pragma unroll
-                    for (int r = 0; r < RB; ++r) {
-                        if (tix[r] < 0) continue;
-                        kahan_add(SE[r], cSE[r], pe[r]);
-                        kahan_add(SB[r], cSB[r], pb[r]);
-                        SV[r] += pv[r];
-                        kahan_add(SW[r], cSW[r], pw[r]);
-                        NM[r] += L;
-                        NN[r] += ring_range_count(a.NPRE, rstart, rnr, jbase + s0 + r + ti.dlo + ti.da, L);
-                    }
+                for (int r = 0; r < RB; ++r) {
+                    if (tix[r] < 0) continue;
+                    kahan_add(SE[r], cSE[r], pe[r]);
+                    kahan_add(SB[r], cSB[r], pb[r]);
+                    SV[r] += pv[r];
+                    kahan_add(SW[r], cSW[r], pw[r]);
+                    NM[r] += L;
+                    const int lo = cur.k0 + s0 + r;
+                    NN[r] += pre[b][ppos(s0 + r + L)] - pre[b][ppos(s0 + r)] +
+                             (wraps(lo + L, cur.nr) - wraps(lo, cur.nr)) * ring_tot;
                 }
             }
             // ---- guard-band offsets: decided per target in float64
-            if (any && ti.namb > 0) {
+            if (any && cur.off >= 0) {
+                const ToeInfo ti = a.toe[row0 + e];
                 for (int ia = 0; ia < ti.namb; ++ia) {
                     const int c = ia == 0 ? ti.amb0 : (ia == 1 ? ti.amb1 : ti.amb2);
                     const float4 G = __ldg(a.toe_geo + ti.off + c);
@@ -445,9 +505,9 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
                     for (int r = 0; r < RB; ++r) {
                         if (tix[r] < 0) continue;
                         const int64_t pix = ring_start0 + jbase + s0 + r;
-                        int kk = (jbase + s0 + r + ti.dlo + c) % rnr;
-                        if (kk < 0) kk += rnr;
-                        const int p = rstart + kk;
+                        int kk = (jbase + s0 + r + ti.dlo + c) % cur.nr;
+                        if (kk < 0) kk += cur.nr;
+                        const int p = cur.start + kk;
                         if (!exact_member(a, pix, p)) continue;
                         const float4 px = __ldg(a.PX + p);
                         kahan_add(SE[r], cSE[r], fmaf(G.x, px.x, G.y * px.y));
@@ -459,13 +519,14 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
                     }
                 }
             }
-            if (L > 0) __syncthreads();   // the staged segment is rewritten by the next ring pair
+            cur = nxt;
         }
+        cp_async_wait_all();
 #pragma unroll
         for (int r = 0; r < RB; ++r)
             if (tix[r] >= 0)
                 finalise(a, tb + tix[r], SE[r], cSE[r], SB[r], cSB[r], SV[r], 0.f, SW[r], cSW[r], NN[r], NM[r]);
-        __syncthreads();   // slot map and s_tile are rewritten by the next tile
+        __syncthreads();   // slot map, buffers and s_tile are rewritten by the next tile
     }
 }
 
