@@ -300,6 +300,85 @@ def run_native_pixel(args, world, rank):
     return res
 
 
+GALAXY_WORKLOADS = {
+    # 5e7 clustered galaxies on a 1,000 deg^2 cap, sorted into NSIDE 4096,
+    # output NSIDE 2048, polynomial filter, 15'
+    "brute2048": dict(n_gal=50_000_000, area_deg2=1000.0, nside_bin=4096, nside_out=2048, theta_ap=15.0,
+                      filt="poly"),
+    # a small case of the same kernels for profiling
+    "brute_small": dict(n_gal=4_000_000, area_deg2=100.0, nside_bin=4096, nside_out=2048, theta_ap=15.0,
+                        filt="poly"),
+}
+# float32 flops per member pair of the brute-force kernel (source count, FMA = 2):
+# offsets 2, latitude series 10, azimuth series 9, chord 3, direction + 2psi 10,
+# filter 8, weight 1, E/B 10, variance + weight 4
+BRUTE_FLOPS_PER_PAIR = {"poly": 57, "schirmer": 62}
+
+
+def run_native_galaxy(args, world, rank):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t_gen = time.perf_counter()
+    wl = workloads.galaxy_workload(dev, api.pix2vec, **GALAXY_WORKLOADS[args.workload])
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    ctx = api.Context(wl.nside_out, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside_bin)
+    ctx.set_targets(wl.targets)
+    cat = wl.cat
+    out = ctx._out(None)[0]
+    stream = torch.cuda.current_stream()
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        ctx.bin_galaxies(cat.ra_deg, cat.dec_deg, cat.e1, cat.e2, cat.w)
+        if evs:
+            evs[1].record(stream)
+        ctx.map_bruteforce(out)
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pairs_step = int(out["members"].sum().item())
+    clocks = Clocks(torch.cuda.current_device())
+    bin_ms, map_ms = [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        step(evs)
+        bin_ms.append(evs)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    total = t0.elapsed_time(t1) / args.steps
+    b_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in bin_ms)
+    m_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in bin_ms)
+    ms_step = max_over_ranks(total, world)
+    value = sum_over_ranks(float(pairs_step), world) / (ms_step * 1e-3) / 1e9
+    flops = BRUTE_FLOPS_PER_PAIR[wl.filter]
+    achieved = pairs_step * flops / (m_ms * 1e-3) / 1e12
+    res = {"metric": METRIC, "value": round(value, 3), "unit": "Gpair/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "desc": wl.desc, "targets": int(wl.targets.numel()),
+                      "galaxies": cat.n, "pairs_per_step": pairs_step,
+                      "l2": "inputs (2.4 GB catalogue) larger than L2; no flush"},
+           "bin_ms": round(b_ms, 3), "map_ms": round(m_ms, 3),
+           "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 2),
+                        "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                        "kernel": "k_map_galaxy", "flops_per_pair": flops},
+           "clocks": ck, "input_gen_s": round(t_gen, 1)}
+    ctx.close()
+    return res
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return None
@@ -335,7 +414,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="pixel4096", choices=sorted(PIXEL_WORKLOADS))
+    ap.add_argument("--workload", default="pixel4096", choices=sorted(PIXEL_WORKLOADS) + sorted(GALAXY_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -343,6 +422,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, world, rank)
+    elif args.workload in GALAXY_WORKLOADS:
+        res = run_native_galaxy(args, world, rank)
     else:
         res = run_native_pixel(args, world, rank)
     if rank == 0 and res is not None:

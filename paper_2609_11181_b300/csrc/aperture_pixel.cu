@@ -126,16 +126,17 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             sin_hav<MODE>(u, sinu, h);
             const float s2 = fmaf(R.B, h, R.A);
             const int p = pbeg + i;
-            if (s2 > a.Thi) continue;
             if (s2 >= a.Tlo) {
-                if (ndef == 0) {
-                    def0 = p;
-                    ud0 = u;
-                } else {
-                    def1 = p;
-                    ud1 = u;
+                if (s2 <= a.Thi) {
+                    if (ndef == 0) {
+                        def0 = p;
+                        ud0 = u;
+                    } else {
+                        def1 = p;
+                        ud1 = u;
+                    }
+                    ++ndef;
                 }
-                ++ndef;
                 continue;
             }
             const float x = R.mrho0 * sinu;

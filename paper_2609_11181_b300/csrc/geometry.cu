@@ -79,7 +79,9 @@ __global__ void k_ring_pairs(int64_t N0, int64_t N1, double theta_disc, double T
             hw = 0.5 * g.nr;
         } else {
             const double half = 2.0 * asin(sqrt(fmax(sn2, 0.0)));
-            hw = half / dphi * (1.0 + 1e-6) + 1.0;
+            // margin: float32 rounding of the window and of the per-pair offsets
+            // is below 1e-4 bin pixels; pixels just outside are tested anyway
+            hw = half / dphi * (1.0 + 1e-5) + 0.01;
             if (2.0 * hw + 1.0 >= (double)g.nr) {
                 flags |= RP_WHOLE | RP_WIDE;
                 hw = 0.5 * g.nr;
