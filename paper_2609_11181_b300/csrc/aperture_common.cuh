@@ -56,12 +56,19 @@ struct MapArgs {
     const int32_t *offsets;
     const float4 *geo, *shear;
     const double2 *radec;
+    const uint32_t *keys;    // pixel of each sorted galaxy
+    double *raw;             // brute force: per target raw sums (SE, SB, SV, SW), float64
+    int32_t *raw_n;          // per target member count
+    void *band;              // guard-band pair list
+    int64_t band_cap;
+    unsigned long long *band_count;
     // outputs
     double *sum_w;
     float *map_e, *map_b, *var;
     int64_t *count;
     int32_t *members;
     unsigned long long *fp64_count;
+    int *status;             // device status word (SMART_STATUS_* bits)
 };
 
 // great-circle separation^2 from the chord^2: d^2 = sum_n 2 s^(2n) / (n^2 C(2n,n))

@@ -598,13 +598,14 @@ __global__ void k_gen_scatter(const int32_t *__restrict__ flag, const int32_t *_
 // tile list of a sorted target list: a new tile starts where the ring or
 // the aligned block of TS azimuth slots changes
 // ------------------------------------------------------------------------
-__global__ void k_tile_flags(const int64_t *__restrict__ t, int64_t n, int64_t N0, int32_t *__restrict__ flag) {
+__global__ void k_tile_flags(const int64_t *__restrict__ t, int64_t n, int64_t N0, int log2_slots,
+                             int32_t *__restrict__ flag) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const RingPix a = pix_to_ring(N0, t[k]);
         int f = 1;
         if (k > 0) {
             const RingPix b = pix_to_ring(N0, t[k - 1]);
-            f = (a.ring != b.ring) || ((a.j >> TS_LOG2) != (b.j >> TS_LOG2));
+            f = (a.ring != b.ring) || ((a.j >> log2_slots) != (b.j >> log2_slots));
         }
         flag[k] = f;
     }
@@ -618,15 +619,15 @@ __global__ void k_tile_scatter(const int32_t *__restrict__ flag, const int32_t *
     }
 }
 
-smart_status build_tiles(smart_ctx *c) {
+smart_status build_tiles_log2(smart_ctx *c, int log2_slots, int64_t **tiles, int64_t *cap, int64_t *n_tiles) {
     const int64_t n = c->n_targets;
-    c->n_tiles = 0;
+    *n_tiles = 0;
     if (n == 0) return SMART_OK;
     smart_status st = ensure_alloc(c, (void **)&c->tile_flag, c->cap_tile_flag, 2 * n + 1, sizeof(int32_t), "tile flags");
     if (st != SMART_OK) return st;
     int32_t *flag = c->tile_flag, *idx = c->tile_flag + n;
     const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 32);
-    k_tile_flags<<<blocks, 256, 0, c->stream>>>(c->targets, n, c->nside_out, flag);
+    k_tile_flags<<<blocks, 256, 0, c->stream>>>(c->targets, n, c->nside_out, log2_slots, flag);
     st = exclusive_scan_i32(c, flag, idx, n, n);
     if (st != SMART_OK) return st;
     int32_t last[2] = {0, 0};
@@ -635,12 +636,14 @@ smart_status build_tiles(smart_ctx *c) {
     st = check_cuda(c, cudaStreamSynchronize(c->stream), "tile count");
     if (st != SMART_OK) return st;
     const int64_t nt = (int64_t)last[0] + last[1];
-    st = ensure_alloc(c, (void **)&c->tiles, c->cap_tiles, nt + 1, sizeof(int64_t), "tiles");
+    st = ensure_alloc(c, (void **)tiles, *cap, nt + 1, sizeof(int64_t), "tiles");
     if (st != SMART_OK) return st;
-    k_tile_scatter<<<blocks, 256, 0, c->stream>>>(flag, idx, n, c->tiles);
-    c->n_tiles = nt;
+    k_tile_scatter<<<blocks, 256, 0, c->stream>>>(flag, idx, n, *tiles);
+    *n_tiles = nt;
     return check_cuda(c, cudaGetLastError(), "tile scatter");
 }
+
+smart_status build_tiles(smart_ctx *c) { return build_tiles_log2(c, TS_LOG2, &c->tiles, &c->cap_tiles, &c->n_tiles); }
 
 // ------------------------------------------------------------------------
 // Schirmer filter table: cubic Hermite pieces of Q on QTAB_BINS uniform bins
@@ -791,6 +794,7 @@ smart_status common_args(smart_ctx *c, const smart_maps *out, MapArgs &a) {
     a.count = out->count;
     a.members = out->members;
     a.fp64_count = c->d_fp64_count;
+    a.status = c->d_status;
     return SMART_OK;
 }
 

@@ -68,6 +68,9 @@ extern "C" smart_status smart_create(int nside_out, const smart_filter *filter, 
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
         c->num_sms = sms;
     if (cudaMalloc(&c->d_fp64_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_band_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_work, sizeof(int)) != cudaSuccess) {
         if (c->d_fp64_count) cudaFree(c->d_fp64_count);
         delete c;
@@ -84,7 +87,8 @@ extern "C" void smart_destroy(smart_ctx *c) {
                     c->own_np, c->keys, c->keys_alt, c->vals, c->vals_alt, c->offsets, c->rec_geo,
                     c->rec_shear, c->rec_radec, c->hist, c->hist_scan, c->scan_tmp, c->ring_lat, c->d_invalid,
                     c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
-                    c->toe_ring, c->gen_list, c->d_fp64_count};
+                    c->toe_ring, c->gen_list, c->gal_tiles, c->raw, c->band, c->d_band_count,
+                    c->d_status, c->d_fp64_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete c;
@@ -104,6 +108,15 @@ extern "C" smart_status smart_sync(smart_ctx *c, double timeout_s) {
             if (dt > timeout_s) return fail(c, SMART_E_TIMEOUT, "smart_sync: deadline passed");
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int status = 0;
+    smart_status st = check_cuda(c, cudaMemcpy(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "smart_sync status");
+    if (st != SMART_OK) return st;
+    if (status) {
+        cudaMemset(c->d_status, 0, sizeof(int));
+        if (status & SMART_STATUS_BAND_OVERFLOW)
+            return fail(c, SMART_E_OVERFLOW, "guard-band pair list overflowed: brute-force map incomplete");
+        return fail(c, SMART_E_INTERNAL, "device status " + std::to_string(status));
     }
     return SMART_OK;
 }

@@ -261,6 +261,9 @@ static_assert(sizeof(RingPair) == 64, "RingPair layout");
 
 enum { RP_SHIFTED = 1, RP_WIDE = 2, RP_WHOLE = 4 };
 
+// bits of the device status word read back by smart_sync
+enum { SMART_STATUS_BAND_OVERFLOW = 1 };
+
 // Per ring pair of the pixel-mode table: where its per-offset geometry sits
 // in the Toeplitz pool (off = -1: not a Toeplitz pair), the candidate
 // offsets [dlo, dlo + ncand), the run [da, da + L) of certain members
@@ -336,6 +339,14 @@ struct smart_ctx {
     int32_t *gen_list = nullptr;                     // targets handled by the general kernel
     int64_t cap_gen_list = 0, n_gen = 0;
     int64_t targets_version = 0, gen_version = -1;
+    int64_t *gal_tiles = nullptr;                    // brute force: groups of up to 4 targets
+    int64_t cap_gal_tiles = 0, n_gal_tiles = 0, gal_tiles_version = -1;
+    double *raw = nullptr;                           // brute force raw sums + counts
+    int64_t cap_raw = 0;
+    void *band = nullptr;                            // guard-band pairs awaiting float64 decisions
+    int64_t cap_band = 0;
+    unsigned long long *d_band_count = nullptr;
+    int *d_status = nullptr;                         // device status word
     int num_sms = 148;
 
     // diagnostics
@@ -358,6 +369,7 @@ smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out,
 
 // aperture_pixel.cu
 smart_status build_tiles(smart_ctx *ctx);
+smart_status build_tiles_log2(smart_ctx *ctx, int log2_slots, int64_t **tiles, int64_t *cap, int64_t *n_tiles);
 
 // context.cu
 smart_status ensure_own_binned_map(smart_ctx *ctx);
