@@ -49,9 +49,10 @@ __device__ __forceinline__ GalRing gal_ring(const RingPair &Rp) {
     return R;
 }
 
-// galaxy-only part of the pair geometry
-__device__ __forceinline__ void gal_setup(const GalRing &R, const float4 &geo, int kg, float &A, float &B, float &C,
-                                          float &D, float &kf) {
+// galaxy-only part of the pair geometry; frg = the galaxy's azimuth on the
+// bin-ring lattice minus its pixel index kg
+__device__ __forceinline__ void gal_setup(const GalRing &R, const float4 &geo, float &A, float &B, float &C,
+                                          float &D, float &frg) {
     const float dl = R.dlat - geo.x;
     if (R.small) {
         const float d2 = dl * dl;
@@ -65,15 +66,17 @@ __device__ __forceinline__ void gal_setup(const GalRing &R, const float4 &geo, i
     }
     B = R.B0 * geo.w;
     D = R.D0 * geo.z;
-    kf = (float)kg + (geo.y + R.fr_shift);
+    frg = geo.y + R.fr_shift;
 }
 
-// azimuth difference (rad) of a galaxy at lattice coordinate kf from a target at X
-__device__ __forceinline__ float gal_u(const GalRing &R, float kf, int Xi, float Xf) {
-    const float half = 0.5f * (float)R.nr;
-    float t = kf - ((float)Xi + Xf);
-    t += t > half ? -(float)R.nr : (t < -half ? (float)R.nr : 0.f);
-    return t * R.dphi;
+// azimuth difference (rad) of a galaxy (pixel kg, fractional lattice offset
+// frg) from a target at lattice position Xi + Xf: the integer part is taken
+// exactly first, so the float32 difference keeps full relative precision
+__device__ __forceinline__ float gal_u(const GalRing &R, int kg, float frg, int Xi, float Xf) {
+    int dk = kg - Xi;
+    const int half = R.nr >> 1;
+    dk += dk > half ? -R.nr : (dk < -half ? R.nr : 0);
+    return ((float)dk + (frg - Xf)) * R.dphi;
 }
 
 // one member pair's contribution
@@ -189,12 +192,12 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
                 const float4 geo = __ldg(a.geo + g);
                 const float4 sh = __ldg(a.shear + g);
                 const int kg = (int)__ldg(a.keys + g) - R.start;
-                float A, B, C, D, kf;
-                gal_setup(R, geo, kg, A, B, C, D, kf);
+                float A, B, C, D, frg;
+                gal_setup(R, geo, A, B, C, D, frg);
 #pragma unroll
                 for (int r = 0; r < GT; ++r) {
                     if (!on[r]) continue;
-                    const float u = gal_u(R, kf, Xi[r], Xf[r]);
+                    const float u = gal_u(R, kg, frg, Xi[r], Xf[r]);
                     float sinu, h;
                     if (R.small) sin_hav_small(u, sinu, h);
                     else sin_hav_wide(u, sinu, h);
@@ -282,10 +285,11 @@ __global__ void k_galaxy_band(const MapArgs a) {
         lattice_position(tr, Rp.nr >> 2, Xi, Xf);
         const float4 geo = a.geo[bp.galaxy];
         const float4 sh = a.shear[bp.galaxy];
-        float A, B, C, D, kf;
-        gal_setup(R, geo, (int)a.keys[bp.galaxy] - R.start, A, B, C, D, kf);
+        float A, B, C, D, frg;
+        gal_setup(R, geo, A, B, C, D, frg);
         float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
-        gal_member<KIND>(a.f, R, gal_u(R, kf, Xi, Xf), A, B, C, D, sh, pe, pb, pv, pw);
+        gal_member<KIND>(a.f, R, gal_u(R, (int)a.keys[bp.galaxy] - R.start, frg, Xi, Xf), A, B, C, D, sh, pe, pb, pv,
+                         pw);
         double *raw = a.raw + 4 * bp.target;
         atomicAdd(raw + 0, (double)pe);
         atomicAdd(raw + 1, (double)pb);

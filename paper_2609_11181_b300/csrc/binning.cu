@@ -5,8 +5,8 @@
 //   2. stable LSD radix sort of (pixel, input index), 8-bit digits;
 //   3. offset table = exclusive scan of the per-pixel counts;
 //   4. galaxy records permuted into sorted order (float32 offsets from the
-//      pixel centre for the aperture kernel, float64 ra/dec for exact
-//      re-decisions);
+//      pixel centre -- latitude in rad, azimuth in pixels of the ring -- for
+//      the aperture kernel, float64 ra/dec for exact re-decisions);
 //   5. per-pixel sums G1, G2, W, S2 and counts, accumulated in sorted order.
 #include <math.h>
 
@@ -250,7 +250,9 @@ __global__ void k_records(int64_t N, const uint32_t *__restrict__ keys, const ui
             const double dd = d - lat_deg[rp.ring];
             float sd, cd;
             sincospif((float)(d / 180.0), &sd, &cd);
-            gr = make_float4((float)(dd * (SMART_PI / 180.0)), (float)(da * (SMART_PI / 180.0)), sd, cd);
+            // latitude offset in rad; azimuth offset in pixels of the galaxy's own ring
+            const RingGeom rg = ring_geom(N, rp.ring);
+            gr = make_float4((float)(dd * (SMART_PI / 180.0)), (float)(da * (double)rg.nr / 360.0), sd, cd);
         }
         geo[i] = gr;
         sh[i] = make_float4(ww * x1, ww * x2, ww, ww * ww * (x1 * x1 + x2 * x2));
