@@ -161,6 +161,41 @@ smart_status smart_map_bruteforce(smart_ctx *ctx, const smart_maps *out);
  */
 smart_status smart_map_pixel(smart_ctx *ctx, const smart_maps *out);
 
+/* ---- batched pixel-based maps ----------------------------------------- */
+
+typedef struct smart_batch smart_batch;
+
+/*
+ * Many pixel-based maps (Sect. 3.2) as one persistent launch.  Each map is a
+ * context prepared for smart_map_pixel (targets and binned data set, all
+ * contexts with the same filter kind); outs[m] receives map m (its device
+ * buffers must stay valid for the life of the batch).  The work of all maps
+ * is split into items (tiles of an output ring, chunks of targets) ordered
+ * longest first and claimed dynamically by resident CTAs.  With autotune != 0
+ * a few launch shapes are timed on this batch (the maps are computed while
+ * tuning) and the fastest is kept; the launch is then captured in a CUDA
+ * graph on cuda_stream.  Binned inputs are read when the graph runs, so
+ * borrowed (packed) maps may change between runs.  Returns SMART_E_ARG for
+ * mixed filter kinds.
+ */
+smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_maps *outs, int n_maps, int autotune,
+                                void *cuda_stream, smart_batch **out);
+
+/* Launch the captured graph on the batch stream (asynchronous). */
+smart_status smart_batch_run(smart_batch *batch);
+
+/* Launch shape chosen (resident CTAs per SM, item order) and the tuned time. */
+smart_status smart_batch_info(const smart_batch *batch, int *ctas_per_sm, int *longest_first,
+                              int64_t *n_items, double *tuned_ms);
+
+const char *smart_batch_last_error(const smart_batch *batch);
+
+/* Waits for the batch stream, then frees the batch (not the contexts). */
+void smart_batch_destroy(smart_batch *batch);
+
+/* One-shot: create (no autotune), run once, destroy.  Synchronous. */
+smart_status smart_map_batched(smart_ctx *const *ctxs, const smart_maps *outs, int n_maps);
+
 /* ---- geometry utilities (Sect. 3, HEALPix RING; stateless) ---------- */
 
 /* pix[k] = RING pixel at nside of (ra_deg[k], dec_deg[k]); bit-exact with

@@ -47,6 +47,13 @@ SIGNATURES = {
     "smart_get_catalog": (_I32, [_VP, _VP, _VP, _VP]),
     "smart_get_binned": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "smart_last_fp64_decisions": (_I64, [_VP]),
+    "smart_batch_create": (_I32, [ctypes.POINTER(_VP), ctypes.POINTER(SmartMaps), _I32, _I32, _VP, ctypes.POINTER(_VP)]),
+    "smart_batch_run": (_I32, [_VP]),
+    "smart_batch_info": (_I32, [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I64),
+                                ctypes.POINTER(_D)]),
+    "smart_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "smart_batch_destroy": (None, [_VP]),
+    "smart_map_batched": (_I32, [ctypes.POINTER(_VP), ctypes.POINTER(SmartMaps), _I32]),
 }
 
 _lib = None

@@ -197,3 +197,47 @@ class Context:
         self._check(self._lib.smart_get_binned(self._h, *(_ptr(x, x.dtype, "b") for x in (G1, G2, W, S2, n_p))),
                     "smart_get_binned")
         return dict(G1=G1, G2=G2, W=W, S2=S2, n=n_p)
+
+
+class Batch:
+    """Many pixel-based maps in one persistent launch replayed from a CUDA graph."""
+
+    def __init__(self, ctxs: list, outs: list | None = None, autotune: bool = True,
+                 stream: torch.cuda.Stream | None = None):
+        self._lib = N.load()
+        self.ctxs = list(ctxs)
+        if outs is None:
+            outs = [None] * len(self.ctxs)
+        pairs = [c._out(o) for c, o in zip(self.ctxs, outs)]
+        self.outs = [p[0] for p in pairs]
+        maps = (N.SmartMaps * len(pairs))(*[p[1] for p in pairs])
+        hs = (ctypes.c_void_p * len(self.ctxs))(*[c._h.value for c in self.ctxs])
+        h = ctypes.c_void_p()
+        st = self._lib.smart_batch_create(hs, maps, len(self.ctxs), 1 if autotune else 0,
+                                          _stream_handle(stream), ctypes.byref(h))
+        if st:
+            raise SmartError(st, "smart_batch_create")
+        self._h = h
+        self._maps = maps
+
+    def run(self):
+        st = self._lib.smart_batch_run(self._h)
+        if st:
+            raise SmartError(st, "smart_batch_run: " + (self._lib.smart_batch_last_error(self._h) or b"").decode())
+        return self.outs
+
+    def info(self) -> dict:
+        cps, lf, ni, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_double()
+        self._lib.smart_batch_info(self._h, ctypes.byref(cps), ctypes.byref(lf), ctypes.byref(ni), ctypes.byref(ms))
+        return dict(ctas_per_sm=cps.value, longest_first=bool(lf.value), n_items=ni.value, tuned_ms=ms.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.smart_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

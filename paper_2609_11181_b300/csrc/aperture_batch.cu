@@ -1,0 +1,313 @@
+// aperture_batch.cu -- many pixel-based maps in one persistent launch,
+// captured in a CUDA graph (batched form of Sect. 3.2).
+//
+// Each map keeps its own context (targets, binned map, aperture, tables).
+// The batch builds one global work list over all maps -- Toeplitz tiles and
+// chunks of 128 general targets -- ordered by estimated cost, longest first,
+// and a persistent kernel claims items with an atomic counter, so maps of
+// very different size and aperture share the SMs without tail effects.  A
+// small autotuner times a few launch shapes (resident CTAs per SM, item
+// order) on the real batch and keeps the fastest; the launch (and the count
+// prefixes of copied binned maps) is then captured once in a CUDA graph and
+// replayed by smart_batch_run.
+#include <math.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "aperture_pixel.cuh"
+
+namespace smart {
+
+struct BatchItem {
+    int64_t index;     // tile index (Toeplitz) or first position in the general list
+    int map;
+    int type;          // 0: Toeplitz tile, 1: chunk of general targets
+    int count;         // targets in a general chunk
+    int pad;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(NT, 4) k_pixel_batched(const MapArgs *__restrict__ maps,
+                                                          const BatchItem *__restrict__ items, int64_t n_items,
+                                                          int *__restrict__ work) {
+    __shared__ __align__(16) ToeShared S;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
+        __syncthreads();
+        const int64_t item = s_item;
+        __syncthreads();   // every thread has read s_item
+        if (item >= n_items) break;
+        const BatchItem it = items[item];
+        const MapArgs &a = maps[it.map];
+        if (it.type == 0) {
+            toeplitz_tile<KIND>(a, it.index, S);
+        } else if ((int)threadIdx.x < it.count) {
+            general_target<KIND>(a, a.gen_list[it.index + threadIdx.x], a.f.qtab);
+        }
+    }
+}
+
+__global__ void k_tiles_wanted(const MapArgs a, unsigned char *__restrict__ want) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.n_tiles; t += (int64_t)gridDim.x * blockDim.x)
+        want[t] = toeplitz_tile_wanted(a, t) ? 1 : 0;
+}
+
+}  // namespace smart
+
+using namespace smart;
+
+struct smart_batch {
+    std::vector<smart_ctx *> ctxs;
+    std::vector<MapArgs> args;
+    std::vector<BatchItem> by_cost, natural;
+    MapArgs *d_maps = nullptr;
+    BatchItem *d_items = nullptr;
+    int64_t n_items = 0;
+    int *d_work = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kind = 0;
+    int ctas_per_sm = 4;
+    int order = 0;            // 0: longest first, 1: natural
+    double tuned_ms = 0.0;
+    std::string err;
+};
+
+static smart_status bfail(smart_batch *b, smart_status st, const std::string &m) {
+    if (b) b->err = m;
+    return st;
+}
+
+// launch the batched kernel (plus the count prefixes) on the batch stream
+static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
+    for (size_t m = 0; m < b->ctxs.size(); ++m) {
+        smart_ctx *c = b->ctxs[m];
+        cudaStream_t keep = c->stream;
+        c->stream = b->stream;
+        smart_status st = launch_count_prefix(c);
+        c->stream = keep;
+        if (st != SMART_OK) return bfail(b, st, "count prefix of map " + std::to_string(m) + ": " + c->err);
+    }
+    if (cudaMemsetAsync(b->d_work, 0, sizeof(int), b->stream) != cudaSuccess)
+        return bfail(b, SMART_E_CUDA, "work counter reset failed");
+    if (b->n_items == 0) return SMART_OK;
+    const int sms = b->ctxs[0]->num_sms;
+    const unsigned grid = (unsigned)std::min<int64_t>(b->n_items, (int64_t)sms * ctas_per_sm);
+    const BatchItem *items = b->d_items + (order == 0 ? 0 : b->n_items);
+    if (b->kind == SMART_FILTER_POLY)
+        k_pixel_batched<SMART_FILTER_POLY><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
+    else
+        k_pixel_batched<SMART_FILTER_SCHIRMER><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, SMART_E_CUDA, std::string("k_pixel_batched: ") + cudaGetErrorString(e));
+    return SMART_OK;
+}
+
+// process-wide memory of tuned launch shapes, keyed by the batch's shape
+static std::map<std::string, std::pair<int, int>> &tune_cache() {
+    static std::map<std::string, std::pair<int, int>> m;
+    return m;
+}
+
+extern "C" void smart_batch_destroy(smart_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_maps) cudaFree(b->d_maps);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_work) cudaFree(b->d_work);
+    delete b;
+}
+
+extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_maps *outs, int n_maps, int autotune,
+                                           void *cuda_stream, smart_batch **out) {
+    if (!out) return SMART_E_ARG;
+    *out = nullptr;
+    if (!ctxs || !outs || n_maps < 1 || n_maps > (1 << 20)) return SMART_E_ARG;
+    smart_batch *b = new (std::nothrow) smart_batch();
+    if (!b) return SMART_E_NOMEM;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->kind = ctxs[0] ? ctxs[0]->filter_kind : 0;
+    for (int m = 0; m < n_maps; ++m) {
+        if (!ctxs[m] || ctxs[m]->filter_kind != b->kind) {
+            delete b;
+            return SMART_E_ARG;          // every map of a batch uses the same filter kind
+        }
+    }
+    b->ctxs.assign(ctxs, ctxs + n_maps);
+    b->args.resize(n_maps);
+    smart_status st = SMART_OK;
+    std::vector<BatchItem> items;
+    std::vector<double> cost;
+    for (int m = 0; m < n_maps && st == SMART_OK; ++m) {
+        smart_ctx *c = ctxs[m];
+        cudaStream_t keep = c->stream;
+        c->stream = b->stream;
+        MapArgs a{};
+        st = prepare_pixel(c, &outs[m], a);
+        if (st != SMART_OK) {
+            b->err = "map " + std::to_string(m) + ": " + c->err;
+            c->stream = keep;
+            break;
+        }
+        a.work = nullptr;
+        a.fp64_count = c->d_fp64_count;
+        b->args[m] = a;
+        // the per-pair cost grows with the number of pixels in an aperture
+        const double pix_per_ap = 3.0 * c->nside_bin * c->nside_bin / SMART_PI * c->area;
+        if (a.n > 0 && a.n_gen < a.n) {
+            std::vector<int64_t> tiles(a.n_tiles + 1);
+            std::vector<unsigned char> want(a.n_tiles);
+            unsigned char *d_want = nullptr;
+            if (cudaMalloc(&d_want, (size_t)std::max<int64_t>(a.n_tiles, 1)) != cudaSuccess) {
+                st = bfail(b, SMART_E_NOMEM, "cudaMalloc(tile flags) failed");
+            } else {
+                k_tiles_wanted<<<(unsigned)std::min<int64_t>((a.n_tiles + 255) / 256, 4096), 256, 0, b->stream>>>(a, d_want);
+                cudaMemcpyAsync(want.data(), d_want, (size_t)a.n_tiles, cudaMemcpyDeviceToHost, b->stream);
+                cudaMemcpyAsync(tiles.data(), a.tiles, (size_t)(a.n_tiles + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream);
+                if (cudaStreamSynchronize(b->stream) != cudaSuccess) st = bfail(b, SMART_E_CUDA, "tile list download failed");
+                cudaFree(d_want);
+            }
+            for (int64_t t = 0; t < a.n_tiles && st == SMART_OK; ++t) {
+                if (!want[t]) continue;
+                BatchItem it{t, m, 0, 0, 0};
+                items.push_back(it);
+                cost.push_back((double)(tiles[t + 1] - tiles[t]) * pix_per_ap);
+            }
+        }
+        for (int64_t g = 0; g < a.n_gen && st == SMART_OK; g += NT) {
+            BatchItem it{g, m, 1, (int)std::min<int64_t>(NT, a.n_gen - g), 0};
+            items.push_back(it);
+            cost.push_back(5.0 * it.count * pix_per_ap);       // general pairs cost ~5x Toeplitz pairs
+        }
+        c->stream = keep;
+    }
+    if (st != SMART_OK) {
+        smart_batch_destroy(b);
+        return st;
+    }
+    b->n_items = (int64_t)items.size();
+    std::vector<int64_t> idx(items.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int64_t)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
+    b->natural = items;
+    b->by_cost.resize(items.size());
+    for (size_t i = 0; i < idx.size(); ++i) b->by_cost[i] = items[idx[i]];
+    const size_t nb = std::max<size_t>(1, items.size());
+    if (cudaMalloc(&b->d_maps, sizeof(MapArgs) * n_maps) != cudaSuccess ||
+        cudaMalloc(&b->d_items, sizeof(BatchItem) * 2 * nb) != cudaSuccess ||
+        cudaMalloc(&b->d_work, sizeof(int)) != cudaSuccess) {
+        smart_batch_destroy(b);
+        return SMART_E_NOMEM;
+    }
+    cudaMemcpyAsync(b->d_maps, b->args.data(), sizeof(MapArgs) * n_maps, cudaMemcpyHostToDevice, b->stream);
+    if (!items.empty()) {
+        cudaMemcpyAsync(b->d_items, b->by_cost.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(b->d_items + items.size(), b->natural.data(), sizeof(BatchItem) * items.size(),
+                        cudaMemcpyHostToDevice, b->stream);
+    }
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        smart_batch_destroy(b);
+        return SMART_E_CUDA;
+    }
+
+    // ---- autotuner: resident CTAs per SM x item order, timed on this batch
+    std::string key = std::to_string(b->kind) + ":" + std::to_string(n_maps) + ":" + std::to_string(b->n_items);
+    for (int m = 0; m < std::min(n_maps, 8); ++m) key += ":" + std::to_string(ctxs[m]->nside_bin) + "/" + std::to_string(ctxs[m]->n_targets);
+    auto hit = tune_cache().find(key);
+    if (hit != tune_cache().end()) {
+        b->ctas_per_sm = hit->second.first;
+        b->order = hit->second.second;
+    } else if (autotune && b->n_items > 0) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        double best = 1e30;
+        const int shapes[] = {2, 3, 4};
+        for (int order = 0; order < 2 && st == SMART_OK; ++order) {
+            for (int cps : shapes) {
+                st = batch_launch(b, cps, order);       // warm
+                if (st != SMART_OK) break;
+                cudaEventRecord(e0, b->stream);
+                st = batch_launch(b, cps, order);
+                if (st != SMART_OK) break;
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = bfail(b, SMART_E_CUDA, "autotune timing failed");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    b->ctas_per_sm = cps;
+                    b->order = order;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != SMART_OK) {
+            smart_batch_destroy(b);
+            return st;
+        }
+        b->tuned_ms = best;
+        tune_cache()[key] = std::make_pair(b->ctas_per_sm, b->order);
+    }
+
+    // ---- capture the launch (count prefixes + batched kernel) in a graph
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        smart_batch_destroy(b);
+        return SMART_E_CUDA;
+    }
+    st = batch_launch(b, b->ctas_per_sm, b->order);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (st != SMART_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        smart_batch_destroy(b);
+        return st != SMART_OK ? st : SMART_E_CUDA;
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+        smart_batch_destroy(b);
+        return SMART_E_CUDA;
+    }
+    *out = b;
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_batch_run(smart_batch *b) {
+    if (!b || !b->exec) return SMART_E_ARG;
+    const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return bfail(b, SMART_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_batch_info(const smart_batch *b, int *ctas_per_sm, int *longest_first,
+                                         int64_t *n_items, double *tuned_ms) {
+    if (!b) return SMART_E_ARG;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (longest_first) *longest_first = b->order == 0;
+    if (n_items) *n_items = b->n_items;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    return SMART_OK;
+}
+
+extern "C" const char *smart_batch_last_error(const smart_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" smart_status smart_map_batched(smart_ctx *const *ctxs, const smart_maps *outs, int n_maps) {
+    if (!ctxs || n_maps < 1 || !ctxs[0]) return SMART_E_ARG;
+    smart_batch *b = nullptr;
+    smart_status st = smart_batch_create(ctxs, outs, n_maps, 0, ctxs[0]->stream, &b);
+    if (st != SMART_OK) return st;
+    st = smart_batch_run(b);
+    smart_batch_destroy(b);          // synchronises the stream
+    return st;
+}

@@ -369,6 +369,9 @@ smart_status exclusive_scan_i32(smart_ctx *ctx, const int32_t *in, int32_t *out,
 
 // aperture_pixel.cu
 smart_status build_tiles(smart_ctx *ctx);
+struct MapArgs;
+smart_status prepare_pixel(smart_ctx *c, const smart_maps *out, MapArgs &a);
+smart_status launch_count_prefix(smart_ctx *c);
 smart_status build_tiles_log2(smart_ctx *ctx, int log2_slots, int64_t **tiles, int64_t *cap, int64_t *n_tiles);
 
 // context.cu
