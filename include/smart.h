@@ -176,7 +176,9 @@ typedef struct smart_batch smart_batch;
  * tuning) and the fastest is kept; the launch is then captured in a CUDA
  * graph on cuda_stream.  Binned inputs are read when the graph runs, so
  * borrowed (packed) maps may change between runs.  Returns SMART_E_ARG for
- * mixed filter kinds.
+ * mixed filter kinds.  A NULL stream means a private stream of the batch
+ * (graphs cannot be captured on the legacy default stream); it orders itself
+ * against the legacy default stream.
  */
 smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_maps *outs, int n_maps, int autotune,
                                 void *cuda_stream, smart_batch **out);
@@ -188,6 +190,7 @@ smart_status smart_batch_run(smart_batch *batch);
 smart_status smart_batch_info(const smart_batch *batch, int *ctas_per_sm, int *longest_first,
                               int64_t *n_items, double *tuned_ms);
 
+/* Last error of a batch; with NULL, why this thread's last smart_batch_create failed. */
 const char *smart_batch_last_error(const smart_batch *batch);
 
 /* Waits for the batch stream, then frees the batch (not the contexts). */

@@ -216,7 +216,8 @@ class Batch:
         st = self._lib.smart_batch_create(hs, maps, len(self.ctxs), 1 if autotune else 0,
                                           _stream_handle(stream), ctypes.byref(h))
         if st:
-            raise SmartError(st, "smart_batch_create")
+            msg = self._lib.smart_batch_last_error(None)
+            raise SmartError(st, "smart_batch_create: " + (msg.decode() if msg else ""))
         self._h = h
         self._maps = maps
 

@@ -71,6 +71,7 @@ struct smart_batch {
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool own_stream = false;
     int kind = 0;
     int ctas_per_sm = 4;
     int order = 0;            // 0: longest first, 1: natural
@@ -78,8 +79,12 @@ struct smart_batch {
     std::string err;
 };
 
+// why the last smart_batch_create of this thread failed (the batch is gone)
+static thread_local std::string g_create_err;
+
 static smart_status bfail(smart_batch *b, smart_status st, const std::string &m) {
     if (b) b->err = m;
+    g_create_err = m;
     return st;
 }
 
@@ -122,6 +127,7 @@ extern "C" void smart_batch_destroy(smart_batch *b) {
     if (b->d_maps) cudaFree(b->d_maps);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_work) cudaFree(b->d_work);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
 
@@ -132,12 +138,23 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     if (!ctxs || !outs || n_maps < 1 || n_maps > (1 << 20)) return SMART_E_ARG;
     smart_batch *b = new (std::nothrow) smart_batch();
     if (!b) return SMART_E_NOMEM;
+    g_create_err.clear();
     b->stream = (cudaStream_t)cuda_stream;
+    if (!b->stream) {
+        // graphs cannot be captured on the legacy default stream: use a
+        // private blocking stream (it orders itself against the legacy stream)
+        if (cudaStreamCreate(&b->stream) != cudaSuccess) {
+            delete b;
+            return SMART_E_CUDA;
+        }
+        b->own_stream = true;
+    }
     b->kind = ctxs[0] ? ctxs[0]->filter_kind : 0;
     for (int m = 0; m < n_maps; ++m) {
         if (!ctxs[m] || ctxs[m]->filter_kind != b->kind) {
-            delete b;
-            return SMART_E_ARG;          // every map of a batch uses the same filter kind
+            bfail(b, SMART_E_ARG, "every map of a batch must use the same filter kind");
+            smart_batch_destroy(b);
+            return SMART_E_ARG;
         }
     }
     b->ctxs.assign(ctxs, ctxs + n_maps);
@@ -203,6 +220,7 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     if (cudaMalloc(&b->d_maps, sizeof(MapArgs) * n_maps) != cudaSuccess ||
         cudaMalloc(&b->d_items, sizeof(BatchItem) * 2 * nb) != cudaSuccess ||
         cudaMalloc(&b->d_work, sizeof(int)) != cudaSuccess) {
+        bfail(b, SMART_E_NOMEM, "cudaMalloc(batch tables) failed");
         smart_batch_destroy(b);
         return SMART_E_NOMEM;
     }
@@ -213,6 +231,7 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
                         cudaMemcpyHostToDevice, b->stream);
     }
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        bfail(b, SMART_E_CUDA, "batch table upload failed");
         smart_batch_destroy(b);
         return SMART_E_CUDA;
     }
@@ -262,20 +281,25 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     }
 
     // ---- capture the launch (count prefixes + batched kernel) in a graph
-    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaError_t ce = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
+        bfail(b, SMART_E_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(ce));
         smart_batch_destroy(b);
         return SMART_E_CUDA;
     }
     st = batch_launch(b, b->ctas_per_sm, b->order);
     cudaGraph_t g = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    ce = cudaStreamEndCapture(b->stream, &g);
     if (st != SMART_OK || ce != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
+        if (st == SMART_OK) bfail(b, SMART_E_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
         smart_batch_destroy(b);
         return st != SMART_OK ? st : SMART_E_CUDA;
     }
     b->graph = g;
-    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    ce = cudaGraphInstantiate(&b->exec, g, 0);
+    if (ce != cudaSuccess) {
+        bfail(b, SMART_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
         smart_batch_destroy(b);
         return SMART_E_CUDA;
     }
@@ -300,7 +324,9 @@ extern "C" smart_status smart_batch_info(const smart_batch *b, int *ctas_per_sm,
     return SMART_OK;
 }
 
-extern "C" const char *smart_batch_last_error(const smart_batch *b) { return b ? b->err.c_str() : "null batch"; }
+extern "C" const char *smart_batch_last_error(const smart_batch *b) {
+    return b ? b->err.c_str() : g_create_err.c_str();
+}
 
 extern "C" smart_status smart_map_batched(smart_ctx *const *ctxs, const smart_maps *outs, int n_maps) {
     if (!ctxs || n_maps < 1 || !ctxs[0]) return SMART_E_ARG;
