@@ -2,14 +2,14 @@
 // captured in a CUDA graph (batched form of Sect. 3.2).
 //
 // Each map keeps its own context (targets, binned map, aperture, tables).
-// The batch builds one global work list over all maps -- Toeplitz tiles and
-// chunks of 128 general targets -- ordered by estimated cost, longest first,
-// and a persistent kernel claims items with an atomic counter, so maps of
-// very different size and aperture share the SMs without tail effects.  A
-// small autotuner times a few launch shapes (resident CTAs per SM, item
-// order) on the real batch and keeps the fastest; the launch (and the count
-// prefixes of copied binned maps) is then captured once in a CUDA graph and
-// replayed by smart_batch_run.
+// The batch builds one global work list of the Toeplitz tiles of all maps,
+// ordered by estimated cost, longest first, which a persistent kernel claims
+// with an atomic counter (maps of very different size and aperture share the
+// SMs without tail effects), and one flat list of the general targets of
+// all maps (one thread each).  A small autotuner times a few launch shapes
+// (resident CTAs per SM, item order) on the real batch and keeps the
+// fastest; the launches (and the count prefixes of copied binned maps) are
+// then captured once in a CUDA graph and replayed by smart_batch_run.
 #include <math.h>
 
 #include <algorithm>
@@ -29,6 +29,7 @@ struct BatchItem {
     int pad;
 };
 
+// the Toeplitz tiles of every map, claimed longest first by resident CTAs
 template <int KIND>
 __global__ void __launch_bounds__(NT, 4) k_pixel_batched(const MapArgs *__restrict__ maps,
                                                           const BatchItem *__restrict__ items, int64_t n_items,
@@ -42,13 +43,19 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_batched(const MapArgs *__restri
         __syncthreads();   // every thread has read s_item
         if (item >= n_items) break;
         const BatchItem it = items[item];
-        const MapArgs &a = maps[it.map];
-        if (it.type == 0) {
-            toeplitz_tile<KIND>(a, it.index, S);
-        } else if ((int)threadIdx.x < it.count) {
-            general_target<KIND>(a, a.gen_list[it.index + threadIdx.x], a.f.qtab);
-        }
+        toeplitz_tile<KIND>(maps[it.map], it.index, S);
     }
+}
+
+// the general targets of every map: one thread per (map, target) entry
+template <int KIND>
+__global__ void __launch_bounds__(128, 6) k_pixel_batched_general(const MapArgs *__restrict__ maps,
+                                                                   const int2 *__restrict__ list, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 e = list[i];
+    const MapArgs &a = maps[e.x];
+    general_target<KIND>(a, e.y, a.f.qtab);
 }
 
 __global__ void k_tiles_wanted(const MapArgs a, unsigned char *__restrict__ want) {
@@ -67,6 +74,8 @@ struct smart_batch {
     MapArgs *d_maps = nullptr;
     BatchItem *d_items = nullptr;
     int64_t n_items = 0;
+    int2 *d_gen = nullptr;           // (map, target) of every general target
+    int64_t n_gen = 0;
     int *d_work = nullptr;
     cudaStream_t stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -100,14 +109,22 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
     }
     if (cudaMemsetAsync(b->d_work, 0, sizeof(int), b->stream) != cudaSuccess)
         return bfail(b, SMART_E_CUDA, "work counter reset failed");
-    if (b->n_items == 0) return SMART_OK;
     const int sms = b->ctxs[0]->num_sms;
-    const unsigned grid = (unsigned)std::min<int64_t>(b->n_items, (int64_t)sms * ctas_per_sm);
-    const BatchItem *items = b->d_items + (order == 0 ? 0 : b->n_items);
-    if (b->kind == SMART_FILTER_POLY)
-        k_pixel_batched<SMART_FILTER_POLY><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
-    else
-        k_pixel_batched<SMART_FILTER_SCHIRMER><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
+    if (b->n_items > 0) {
+        const unsigned grid = (unsigned)std::min<int64_t>(b->n_items, (int64_t)sms * ctas_per_sm);
+        const BatchItem *items = b->d_items + (order == 0 ? 0 : b->n_items);
+        if (b->kind == SMART_FILTER_POLY)
+            k_pixel_batched<SMART_FILTER_POLY><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
+        else
+            k_pixel_batched<SMART_FILTER_SCHIRMER><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
+    }
+    if (b->n_gen > 0) {
+        const unsigned grid = (unsigned)((b->n_gen + 127) / 128);
+        if (b->kind == SMART_FILTER_POLY)
+            k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, b->stream>>>(b->d_maps, b->d_gen, b->n_gen);
+        else
+            k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, b->stream>>>(b->d_maps, b->d_gen, b->n_gen);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(b, SMART_E_CUDA, std::string("k_pixel_batched: ") + cudaGetErrorString(e));
     return SMART_OK;
@@ -126,6 +143,7 @@ extern "C" void smart_batch_destroy(smart_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_maps) cudaFree(b->d_maps);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_gen) cudaFree(b->d_gen);
     if (b->d_work) cudaFree(b->d_work);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
@@ -162,6 +180,7 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     smart_status st = SMART_OK;
     std::vector<BatchItem> items;
     std::vector<double> cost;
+    std::vector<int2> gen;
     for (int m = 0; m < n_maps && st == SMART_OK; ++m) {
         smart_ctx *c = ctxs[m];
         cudaStream_t keep = c->stream;
@@ -198,10 +217,11 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
                 cost.push_back((double)(tiles[t + 1] - tiles[t]) * pix_per_ap);
             }
         }
-        for (int64_t g = 0; g < a.n_gen && st == SMART_OK; g += NT) {
-            BatchItem it{g, m, 1, (int)std::min<int64_t>(NT, a.n_gen - g), 0};
-            items.push_back(it);
-            cost.push_back(5.0 * it.count * pix_per_ap);       // general pairs cost ~5x Toeplitz pairs
+        if (a.n_gen > 0 && st == SMART_OK) {
+            std::vector<int32_t> gl(a.n_gen);
+            cudaMemcpyAsync(gl.data(), a.gen_list, (size_t)a.n_gen * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream);
+            if (cudaStreamSynchronize(b->stream) != cudaSuccess) st = bfail(b, SMART_E_CUDA, "general list download failed");
+            for (int64_t g = 0; g < a.n_gen && st == SMART_OK; ++g) gen.push_back(make_int2(m, gl[g]));
         }
         c->stream = keep;
     }
@@ -217,14 +237,18 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     b->by_cost.resize(items.size());
     for (size_t i = 0; i < idx.size(); ++i) b->by_cost[i] = items[idx[i]];
     const size_t nb = std::max<size_t>(1, items.size());
+    b->n_gen = (int64_t)gen.size();
     if (cudaMalloc(&b->d_maps, sizeof(MapArgs) * n_maps) != cudaSuccess ||
         cudaMalloc(&b->d_items, sizeof(BatchItem) * 2 * nb) != cudaSuccess ||
+        cudaMalloc(&b->d_gen, sizeof(int2) * std::max<size_t>(1, gen.size())) != cudaSuccess ||
         cudaMalloc(&b->d_work, sizeof(int)) != cudaSuccess) {
         bfail(b, SMART_E_NOMEM, "cudaMalloc(batch tables) failed");
         smart_batch_destroy(b);
         return SMART_E_NOMEM;
     }
     cudaMemcpyAsync(b->d_maps, b->args.data(), sizeof(MapArgs) * n_maps, cudaMemcpyHostToDevice, b->stream);
+    if (!gen.empty())
+        cudaMemcpyAsync(b->d_gen, gen.data(), sizeof(int2) * gen.size(), cudaMemcpyHostToDevice, b->stream);
     if (!items.empty()) {
         cudaMemcpyAsync(b->d_items, b->by_cost.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_items + items.size(), b->natural.data(), sizeof(BatchItem) * items.size(),
@@ -243,7 +267,7 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     if (hit != tune_cache().end()) {
         b->ctas_per_sm = hit->second.first;
         b->order = hit->second.second;
-    } else if (autotune && b->n_items > 0) {
+    } else if (autotune && b->n_items + b->n_gen > 0) {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
