@@ -232,6 +232,45 @@ smart_status smart_get_binned(smart_ctx *ctx, float *G1, float *G2, float *W,
    decided in float64 by the last map call (host value; syncs the stream). */
 int64_t smart_last_fp64_decisions(smart_ctx *ctx);
 
+/* ---- catalogue sort without device allocation ---------------------- */
+
+/*
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc or cudaFree when they need a sort: code that
+ * runs inside a fixed device-memory budget handed out by its own pool, host
+ * threads that must not take the device-wide synchronisation those calls
+ * imply, and runtimes that forbid allocation inside their scheduling
+ * regions.  It computes the same sort as smart_bin_galaxies without a
+ * context: the pixel key of every galaxy (RING, nside), a stable radix sort
+ * by key, and the offsets of each pixel's run.
+ *
+ *   nside    power of two in [1, 8192]
+ *   ra, dec  n galaxy positions in degrees (device, f64)
+ *   n        0 <= n <= 1048576 (2^20); larger n returns SMART_E_OVERFLOW
+ *   pix      out, n entries (device): pixel of the galaxy at sorted position i
+ *   perm     out, n entries (device): input index of that galaxy
+ *   offsets  out, 12 nside^2 + 1 entries (device): sorted position of the
+ *            first galaxy of pixel p; offsets[12 nside^2] = valid galaxies.
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ *
+ * Galaxies with non-finite ra/dec or |dec| > 90 get the key 12 nside^2 and
+ * sort after every pixel; they are not reported as an error here.
+ *
+ * The call allocates nothing.  Its working memory is one fixed array of
+ * about 10.5 MB in the library's own device data, held by every GPU that
+ * loads the library until the process exits.  The first call on each device
+ * looks up that array's device address with that device current; make that
+ * first call before any stream capture.  All calls share the array, and it
+ * keeps the last call's contents: calls that overlap on the GPU (on two
+ * streams, or from two host threads, without ordering between them) race and
+ * give wrong results.  The work is enqueued on the stream and the call
+ * returns without waiting; SMART_E_ARG / SMART_E_OVERFLOW are returned
+ * before anything is enqueued, SMART_E_CUDA on a launch or look-up failure.
+ */
+smart_status smart_sort_catalog_noalloc(int nside, const double *ra, const double *dec,
+                                        int64_t n, uint32_t *pix, uint32_t *perm,
+                                        int32_t *offsets, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,7 @@ SIGNATURES = {
     "smart_batch_last_error": (ctypes.c_char_p, [_VP]),
     "smart_batch_destroy": (None, [_VP]),
     "smart_map_batched": (_I32, [ctypes.POINTER(_VP), ctypes.POINTER(SmartMaps), _I32]),
+    "smart_sort_catalog_noalloc": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
 }
 
 _lib = None

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "smart_internal.cuh"
 
@@ -438,4 +439,122 @@ extern "C" smart_status smart_get_binned(smart_ctx *c, float *G1, float *G2, flo
     const int64_t npix = npix_of(c->nside_bin);
     k_unpack<<<grid_for(npix, 256), 256, 0, c->stream>>>(c->PX, c->NP, npix, G1, G2, W, S2, n_p);
     return check_cuda(c, cudaGetLastError(), "smart_get_binned");
+}
+
+// ---------------------------------------------------------------------------
+// Catalogue sort that allocates no device memory.
+//
+// Some callers cannot allocate device memory at the moment they need a sort:
+// code that runs while a fixed memory budget is already committed (every
+// byte handed out by a pool that may not grow), host threads that must not
+// call cudaMalloc/cudaFree because those calls synchronise the whole device,
+// and runtimes that forbid allocations inside their own scheduling regions.
+// For them the sort below works entirely in the caller's output arrays plus
+// one file-scope device scratch array of fixed size, reserved on every GPU
+// that loads this library for as long as the process lives.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NOALLOC_MAX_GALAXIES = int64_t(1) << 20;                  // per call
+constexpr int64_t NOALLOC_MAX_TILES = NOALLOC_MAX_GALAXIES / SORT_TILE;    // radix tiles
+constexpr int64_t NOALLOC_SCAN_INTS = 512 * 1024;                          // scan block sums
+constexpr size_t NOALLOC_KEYS_OFF = 0;
+constexpr size_t NOALLOC_VALS_OFF = NOALLOC_KEYS_OFF + sizeof(uint32_t) * NOALLOC_MAX_GALAXIES;
+constexpr size_t NOALLOC_HIST_OFF = NOALLOC_VALS_OFF + sizeof(uint32_t) * NOALLOC_MAX_GALAXIES;
+constexpr size_t NOALLOC_HSCAN_OFF = NOALLOC_HIST_OFF + sizeof(uint32_t) * RADIX * NOALLOC_MAX_TILES;
+constexpr size_t NOALLOC_SCAN_OFF = NOALLOC_HSCAN_OFF + sizeof(int32_t) * RADIX * NOALLOC_MAX_TILES;
+constexpr size_t NOALLOC_FLAG_OFF = NOALLOC_SCAN_OFF + sizeof(int32_t) * NOALLOC_SCAN_INTS;
+constexpr size_t NOALLOC_BYTES = NOALLOC_FLAG_OFF + 256;
+
+// about 10.5 MB on every device that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// device address of the scratch array on each device (host code cannot use
+// the symbol itself: on the host it is only a stand-in)
+std::mutex g_noalloc_mutex;
+unsigned char *g_noalloc_ptr[256] = {nullptr};
+
+smart_status noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SMART_E_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SMART_E_CUDA;
+        g_noalloc_ptr[dev] = (unsigned char *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SMART_OK;
+}
+
+// exclusive scan with block sums in the scratch array (same kernels as the
+// context path)
+template <typename T>
+smart_status noalloc_scan(const T *in, int64_t n_in, int32_t *out, int64_t n, int32_t *tmp, int64_t tmp_cap,
+                          cudaStream_t s) {
+    if (n <= 0) return SMART_OK;
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 1) {
+        k_scan_tile<T><<<1, SCAN_THREADS, 0, s>>>(in, n_in, out, n, nullptr);
+        return cudaGetLastError() == cudaSuccess ? SMART_OK : SMART_E_CUDA;
+    }
+    if (nb + 1 > tmp_cap) return SMART_E_INTERNAL;     // cannot happen within the stated limits
+    k_scan_tile<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n_in, out, n, tmp);
+    if (cudaGetLastError() != cudaSuccess) return SMART_E_CUDA;
+    const smart_status st = noalloc_scan<int32_t>(tmp, nb, tmp, nb, tmp + nb, tmp_cap - nb, s);
+    if (st != SMART_OK) return st;
+    k_scan_add<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(out, n, tmp);
+    return cudaGetLastError() == cudaSuccess ? SMART_OK : SMART_E_CUDA;
+}
+
+}  // namespace
+
+extern "C" smart_status smart_sort_catalog_noalloc(int nside, const double *ra, const double *dec, int64_t n,
+                                                   uint32_t *pix, uint32_t *perm, int32_t *offsets,
+                                                   void *cuda_stream) {
+    if (!(nside >= 1 && nside <= 8192 && (nside & (nside - 1)) == 0)) return SMART_E_ARG;
+    if (n < 0 || !offsets || (n > 0 && (!ra || !dec || !pix || !perm))) return SMART_E_ARG;
+    if (n > NOALLOC_MAX_GALAXIES) return SMART_E_OVERFLOW;
+    unsigned char *scr = nullptr;
+    smart_status st = noalloc_scratch(&scr);
+    if (st != SMART_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t N = nside;
+    const int64_t npix = npix_of(N);
+    uint32_t *keys_alt = (uint32_t *)(scr + NOALLOC_KEYS_OFF);
+    uint32_t *vals_alt = (uint32_t *)(scr + NOALLOC_VALS_OFF);
+    uint32_t *hist = (uint32_t *)(scr + NOALLOC_HIST_OFF);
+    int32_t *hscan = (int32_t *)(scr + NOALLOC_HSCAN_OFF);
+    int32_t *tmp = (int32_t *)(scr + NOALLOC_SCAN_OFF);
+    int *invalid = (int *)(scr + NOALLOC_FLAG_OFF);      // counted but never read
+    int bits = 0;
+    while (((int64_t)1 << bits) <= npix) ++bits;          // keys go up to npix (sentinel)
+    // the per-pixel counts are accumulated in place in offsets and must start
+    // at zero; every other scratch word is written before it is read
+    if (cudaMemsetAsync(offsets, 0, (size_t)(npix + 1) * sizeof(int32_t), s) != cudaSuccess) return SMART_E_CUDA;
+    if (n > 0) {
+        const int64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+        k_keys<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, pix, perm, invalid);
+        if (cudaGetLastError() != cudaSuccess) return SMART_E_CUDA;
+        uint32_t *ki = pix, *ko = keys_alt, *vi = perm, *vo = vals_alt;
+        for (int shift = 0; shift < bits; shift += RADIX_BITS) {
+            k_radix_hist<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, n, shift, ntiles, hist);
+            st = noalloc_scan<uint32_t>(hist, RADIX * ntiles, hscan, RADIX * ntiles, tmp, NOALLOC_SCAN_INTS, s);
+            if (st != SMART_OK) return st;
+            k_radix_scatter<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, vi, ko, vo, n, shift, ntiles,
+                                                                     (const uint32_t *)hscan);
+            if (cudaGetLastError() != cudaSuccess) return SMART_E_CUDA;
+            std::swap(ki, ko);
+            std::swap(vi, vo);
+        }
+        if (ki != pix) {          // an odd number of passes left the result in the scratch
+            if (cudaMemcpyAsync(pix, ki, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(perm, vi, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return SMART_E_CUDA;
+        }
+        k_run_counts<<<grid_for(n, 256), 256, 0, s>>>(pix, n, (uint32_t)npix, offsets);
+        if (cudaGetLastError() != cudaSuccess) return SMART_E_CUDA;
+    }
+    // offsets[0..npix] = exclusive scan of the counts, in place
+    return noalloc_scan<int32_t>(offsets, npix + 1, offsets, npix + 1, tmp, NOALLOC_SCAN_INTS, s);
 }
