@@ -46,6 +46,7 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12     # 148 SMs x 128 FP32 lanes
 # chord 2, tangent-plane direction + cos/sin 2psi 10, chord->separation series 9,
 # Schirmer filter 15, weight 1, E/B 10, variance + weight 4.
 FLOPS_PER_PAIR = {"schirmer": 68, "poly": 56}
+PEAK_SOURCE = "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (recipe unit counts and maximum SM clock)"
 
 
 def _env_int(k, d):
@@ -150,6 +151,76 @@ def load_peaks():
     return None
 
 
+SCAN_TILE = 2048          # elements per block of the library's exclusive scan
+
+
+def scan_launches(n: int) -> int:
+    """Kernel launches of the library's exclusive scan over n elements: one
+    tile pass, a scan of the block sums (recursively), one add pass."""
+    if n <= 0:
+        return 0
+    nb = -(-n // SCAN_TILE)
+    return 1 if nb == 1 else 2 + scan_launches(nb)
+
+
+def _sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` at `workload` from the committed ncu
+    summary profiles/<kernel>_<workload>.md, or None when there is none or
+    when the kernel's sources changed since the counters were taken (the
+    summary records the sha256 of the source files it covers)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.lstrip().startswith("- "):
+            k, v = line.lstrip()[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    try:
+        srcs = fields["sources"].split()
+        if _sha256(srcs) != fields["source_sha256"]:
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError, OSError):
+        return None
+
+
+def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_source: str):
+    """Roofline of the dominant kernel from the context's per-launch events.
+
+    kernels: {name: (pairs per launch, flops per pair, kernel symbol)}.  The
+    dominant kernel is the one with the largest summed time over the timed
+    steps; achieved = algorithmic flops per launch / its mean launch time."""
+    per = {}
+    for name, (pairs, fpp, sym) in kernels.items():
+        n, ms = ctx.timing_read(name)
+        if n == 0:
+            continue
+        per[name] = {"kernel": sym, "launches": n, "total_ms": round(ms, 3), "ms_per_launch": round(ms / n, 4),
+                     "pairs_per_launch": int(pairs), "flops_per_pair": fpp,
+                     "tflops": round(pairs * fpp / (ms / n * 1e-3) / 1e12, 2) if ms > 0 else None}
+    if not per:
+        return None, per
+    dom = max(per, key=lambda k: per[k]["total_ms"])
+    d = per[dom]
+    achieved = d["tflops"]
+    roof = {"bound": "alu", "achieved": achieved, "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4), "traffic": profiled_traffic(d["kernel"], workload),
+            "kernel": d["kernel"], "launches": d["launches"], "ms_per_launch": d["ms_per_launch"],
+            "pairs_per_launch": d["pairs_per_launch"], "flops_per_pair": d["flops_per_pair"],
+            "peak_source": peak_source}
+    return roof, per
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline: the float64 oracle on a bounded sample of the same targets
 # ---------------------------------------------------------------------------
@@ -215,12 +286,16 @@ def run_native_pixel(args, world, rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    pairs_step = int(out["members"].sum().item())
+    members = out["members"].long()
+    pairs_step = int(members.sum().item())
+    gen_idx = ctx.general_targets()
+    pairs_gen = int(members[gen_idx].sum().item()) if gen_idx.numel() else 0
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(torch.cuda.current_device())
     barrier(world)
     torch.cuda.synchronize()
+    ctx.timing(True)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -237,6 +312,14 @@ def run_native_pixel(args, world, rank):
     ms_step = max_over_ranks(total_ms / args.steps, world)
     pairs_all = sum_over_ranks(float(pairs_step), world)
     value = pairs_all / (ms_step * 1e-3) / 1e9
+    flops = FLOPS_PER_PAIR[wl.filter]
+    roof, per_kernel = kernel_roofline(
+        ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, flops, "k_pixel_toeplitz"),
+              "pixel_general": (pairs_gen, flops, "k_pixel_general")},
+        args.workload, FP32_PEAK_TFLOPS, PEAK_SOURCE)
+    ctx.timing(False)
+    npix_bin = 12 * wl.nside ** 2
+    launches_step = sum(v["launches"] for v in per_kernel.values()) / args.steps + scan_launches(npix_bin + 1)
 
     # end to end through the public API: host (pinned) -> device inputs, map, results -> host
     host_in = [x.cpu().pin_memory() for x in inputs]
@@ -266,13 +349,7 @@ def run_native_pixel(args, world, rank):
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e_steps, world)
 
     peaks = load_peaks()
-    flops = FLOPS_PER_PAIR[wl.filter]
     kmean = statistics.mean(kern_ms)
-    achieved = pairs_step * flops / (kmean * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-            "kernel": "k_map_pixel", "flops_per_pair": flops,
-            "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (recipe unit counts and max clock)"}
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gpair/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
@@ -283,11 +360,12 @@ def run_native_pixel(args, world, rank):
                          "arrays) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "map_time_ms": round(ms_step, 3),
-        "kernel_ms_mean": round(kmean, 3),
+        "step_ms_mean": round(kmean, 3),
         "roofline": roof,
+        "kernels": per_kernel,
         "e2e": {"value": round(pairs_all / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gpair/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3)},
-        "gpu_launches": args.steps,
+        "gpu_launches": int(round(launches_step * args.steps)),
         "clocks": ck,
         "input_gen_s": round(t_gen, 1),
     }
@@ -341,11 +419,12 @@ def run_native_galaxy(args, world, rank):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    pairs_step = int(out["members"].sum().item())
+    pairs_step = int(out["members"].long().sum().item())
     clocks = Clocks(torch.cuda.current_device())
-    bin_ms, map_ms = [], []
+    bin_ms = []
     barrier(world)
     torch.cuda.synchronize()
+    ctx.timing(True)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -363,7 +442,21 @@ def run_native_galaxy(args, world, rank):
     ms_step = max_over_ranks(total, world)
     value = sum_over_ranks(float(pairs_step), world) / (ms_step * 1e-3) / 1e9
     flops = BRUTE_FLOPS_PER_PAIR[wl.filter]
-    achieved = pairs_step * flops / (m_ms * 1e-3) / 1e12
+    roof, per_kernel = kernel_roofline(ctx, {"galaxy": (pairs_step, flops, "k_map_galaxy")}, args.workload,
+                                       FP32_PEAK_TFLOPS, PEAK_SOURCE)
+    phases = {}
+    for name in ("bin_keys", "bin_sort", "bin_records", "bin_pixel_sums", "galaxy_band", "galaxy_finalise"):
+        nl, ms = ctx.timing_read(name)
+        if nl:
+            phases[name] = {"launches": nl, "ms_per_launch": round(ms / nl, 4)}
+    ctx.timing(False)
+    # launches per step: keys, 4 radix passes of (histogram, scan, scatter), run counts,
+    # offsets scan, records, pixel sums; then the three brute-force kernels
+    n_gal = cat.n
+    ntiles = max(1, -(-n_gal // 4096))
+    npix_bin = 12 * wl.nside_bin ** 2
+    passes = -(-(npix_bin).bit_length() // 8)
+    launches_step = (1 + passes * (2 + scan_launches(256 * ntiles)) + 1 + scan_launches(npix_bin + 1) + 2 + 3)
     res = {"metric": METRIC, "value": round(value, 3), "unit": "Gpair/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -371,9 +464,8 @@ def run_native_galaxy(args, world, rank):
                       "galaxies": cat.n, "pairs_per_step": pairs_step,
                       "l2": "inputs (2.4 GB catalogue) larger than L2; no flush"},
            "bin_ms": round(b_ms, 3), "map_ms": round(m_ms, 3),
-           "roofline": {"bound": "alu", "achieved": round(achieved, 2), "peak": round(FP32_PEAK_TFLOPS, 2),
-                        "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
-                        "kernel": "k_map_galaxy", "flops_per_pair": flops},
+           "roofline": roof, "kernels": per_kernel, "phases": phases,
+           "gpu_launches": launches_step * args.steps,
            "clocks": ck, "input_gen_s": round(t_gen, 1)}
     ctx.close()
     return res

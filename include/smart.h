@@ -232,6 +232,47 @@ smart_status smart_get_binned(smart_ctx *ctx, float *G1, float *G2, float *W,
    decided in float64 by the last map call (host value; syncs the stream). */
 int64_t smart_last_fp64_decisions(smart_ctx *ctx);
 
+/* ---- kernel timing (diagnostics; not part of the method) ------------ */
+
+/* Kernels and phases whose launches can be timed. */
+typedef enum {
+    SMART_KT_PIXEL_TOEPLITZ = 0,   /* pixel mode, rings of equal-length ring pairs */
+    SMART_KT_PIXEL_GENERAL = 1,    /* pixel mode, the other targets */
+    SMART_KT_GALAXY = 2,           /* brute force, main kernel */
+    SMART_KT_GALAXY_BAND = 3,      /* brute force, float64 decisions of guard-band pairs */
+    SMART_KT_GALAXY_FINALISE = 4,  /* brute force, normalisation */
+    SMART_KT_BIN_KEYS = 5,         /* smart_bin_galaxies: pixel keys (ang2pix) */
+    SMART_KT_BIN_SORT = 6,         /* smart_bin_galaxies: every radix pass */
+    SMART_KT_BIN_RECORDS = 7,      /* smart_bin_galaxies: permuted galaxy records */
+    SMART_KT_BIN_PIXEL_SUMS = 8,   /* smart_bin_galaxies: per-pixel sums */
+    SMART_KT_COUNT = 9
+} smart_kernel_id;
+
+/*
+ * enable != 0: start a fresh timing record; from now on every launch of the
+ * kernels above made through this context is bracketed by two CUDA events
+ * recorded on the context stream.  enable == 0: stop and discard the record.
+ * Events are created on first use (cudaEventCreate) and reused.
+ */
+smart_status smart_timing_enable(smart_ctx *ctx, int enable);
+
+/*
+ * Number of recorded launches of `kernel` and their summed duration in ms
+ * (host outputs).  Waits for the recorded events, polling with a deadline of
+ * timeout_s seconds (<= 0: no deadline); SMART_E_TIMEOUT if it passes.
+ */
+smart_status smart_timing_read(smart_ctx *ctx, int kernel, int64_t *launches, double *total_ms,
+                               double timeout_s);
+
+/*
+ * Positions (into the target array) of the targets that the last pixel map
+ * sent to the general kernel; the others went to the Toeplitz kernel.
+ * *n_gen (host) receives their number; idx (device, int32, capacity cap)
+ * receives the positions unless NULL.  SMART_E_STATE before the first pixel
+ * map after smart_set_targets.  Asynchronous on the context stream.
+ */
+smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_gen);
+
 /* ---- catalogue sort without device allocation ---------------------- */
 
 /*

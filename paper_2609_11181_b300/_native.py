@@ -15,6 +15,9 @@ LIB_PATH = os.path.join(HERE, "_lib", "libsmart.so")
 STATUS = {0: "SMART_OK", 1: "SMART_E_ARG", 2: "SMART_E_NOMEM", 3: "SMART_E_CUDA", 4: "SMART_E_STATE",
           5: "SMART_E_TIMEOUT", 6: "SMART_E_OVERFLOW", 7: "SMART_E_INTERNAL"}
 
+KERNELS = {"pixel_toeplitz": 0, "pixel_general": 1, "galaxy": 2, "galaxy_band": 3, "galaxy_finalise": 4,
+           "bin_keys": 5, "bin_sort": 6, "bin_records": 7, "bin_pixel_sums": 8}
+
 FILTER_POLY = 1
 FILTER_SCHIRMER = 2
 
@@ -54,6 +57,9 @@ SIGNATURES = {
     "smart_batch_last_error": (ctypes.c_char_p, [_VP]),
     "smart_batch_destroy": (None, [_VP]),
     "smart_map_batched": (_I32, [ctypes.POINTER(_VP), ctypes.POINTER(SmartMaps), _I32]),
+    "smart_timing_enable": (_I32, [_VP, _I32]),
+    "smart_timing_read": (_I32, [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), _D]),
+    "smart_get_general_targets": (_I32, [_VP, _VP, _I64, ctypes.POINTER(_I64)]),
     "smart_sort_catalog_noalloc": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
 }
 

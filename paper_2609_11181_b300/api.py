@@ -178,6 +178,31 @@ class Context:
     def fp64_decisions(self) -> int:
         return int(self._lib.smart_last_fp64_decisions(self._h))
 
+    # -- kernel timing
+    def timing(self, enable: bool = True):
+        """Start (or stop and discard) the per-kernel event record of this context."""
+        self._check(self._lib.smart_timing_enable(self._h, 1 if enable else 0), "smart_timing_enable")
+
+    def timing_read(self, kernel: str, timeout_s: float = 60.0):
+        """(launches, summed ms) of one kernel since timing(True); kernel names as in _native.KERNELS."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        self._check(self._lib.smart_timing_read(self._h, N.KERNELS[kernel], ctypes.byref(n), ctypes.byref(ms),
+                                                float(timeout_s)), "smart_timing_read")
+        return int(n.value), float(ms.value)
+
+    def general_targets(self) -> torch.Tensor:
+        """Positions of the targets the last pixel map sent to the general kernel (int64, device)."""
+        ng = ctypes.c_int64()
+        self._check(self._lib.smart_get_general_targets(self._h, None, 0, ctypes.byref(ng)),
+                    "smart_get_general_targets")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        idx = torch.empty(int(ng.value), dtype=torch.int32, device=dev)
+        if idx.numel():
+            self._check(self._lib.smart_get_general_targets(self._h, _ptr(idx, torch.int32, "idx"), idx.numel(),
+                                                            ctypes.byref(ng)), "smart_get_general_targets")
+        self.sync(60)
+        return idx.long()
+
     # -- inspection
     def get_catalog(self, n: int):
         dev = torch.device("cuda", torch.cuda.current_device())

@@ -366,14 +366,20 @@ extern "C" smart_status smart_map_bruteforce(smart_ctx *c, const smart_maps *out
     cudaMemsetAsync(c->d_band_count, 0, sizeof(unsigned long long), c->stream);
     if (n == 0) return SMART_OK;
     const unsigned blocks = (unsigned)((a.n_tiles + GW - 1) / GW);
-    if (c->filter_kind == SMART_FILTER_POLY) {
-        k_map_galaxy<SMART_FILTER_POLY><<<blocks, 32 * GW, 0, c->stream>>>(a);
-        k_galaxy_band<SMART_FILTER_POLY><<<(unsigned)c->num_sms, 256, 0, c->stream>>>(a);
-    } else {
-        k_map_galaxy<SMART_FILTER_SCHIRMER><<<blocks, 32 * GW, 0, c->stream>>>(a);
-        k_galaxy_band<SMART_FILTER_SCHIRMER><<<(unsigned)c->num_sms, 256, 0, c->stream>>>(a);
+    {
+        KernelTimer timer(c, SMART_KT_GALAXY);
+        if (c->filter_kind == SMART_FILTER_POLY) k_map_galaxy<SMART_FILTER_POLY><<<blocks, 32 * GW, 0, c->stream>>>(a);
+        else k_map_galaxy<SMART_FILTER_SCHIRMER><<<blocks, 32 * GW, 0, c->stream>>>(a);
+    }
+    {
+        KernelTimer timer(c, SMART_KT_GALAXY_BAND);
+        if (c->filter_kind == SMART_FILTER_POLY) k_galaxy_band<SMART_FILTER_POLY><<<(unsigned)c->num_sms, 256, 0, c->stream>>>(a);
+        else k_galaxy_band<SMART_FILTER_SCHIRMER><<<(unsigned)c->num_sms, 256, 0, c->stream>>>(a);
     }
     const unsigned fb = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 16);
-    k_galaxy_finalise<<<fb, 256, 0, c->stream>>>(a);
+    {
+        KernelTimer timer(c, SMART_KT_GALAXY_FINALISE);
+        k_galaxy_finalise<<<fb, 256, 0, c->stream>>>(a);
+    }
     return check_cuda(c, cudaGetLastError(), "brute-force launches");
 }

@@ -476,6 +476,7 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     if (st != SMART_OK || a.n == 0) return st;
     if (a.n_gen < a.n) {
         const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * 4);
+        KernelTimer timer(c, SMART_KT_PIXEL_TOEPLITZ);
         if (c->filter_kind == SMART_FILTER_POLY) k_pixel_toeplitz<SMART_FILTER_POLY><<<grid, NT, 0, c->stream>>>(a);
         else k_pixel_toeplitz<SMART_FILTER_SCHIRMER><<<grid, NT, 0, c->stream>>>(a);
         st = check_cuda(c, cudaGetLastError(), "k_pixel_toeplitz launch");
@@ -483,6 +484,7 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     }
     if (a.n_gen > 0) {
         const unsigned grid = (unsigned)((a.n_gen + 127) / 128);
+        KernelTimer timer(c, SMART_KT_PIXEL_GENERAL);
         if (c->filter_kind == SMART_FILTER_POLY) k_pixel_general<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a);
         else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a);
         st = check_cuda(c, cudaGetLastError(), "k_pixel_general launch");

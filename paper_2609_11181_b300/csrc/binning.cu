@@ -344,9 +344,13 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     cudaStream_t s = c->stream;
     cudaMemsetAsync(c->d_invalid, 0, sizeof(int), s);
     if (n > 0) {
-        k_keys<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, c->keys, c->vals, c->d_invalid);
+        {
+            KernelTimer timer(c, SMART_KT_BIN_KEYS);
+            k_keys<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, c->keys, c->vals, c->d_invalid);
+        }
         if ((st = check_cuda(c, cudaGetLastError(), "k_keys")) != SMART_OK) return st;
         uint32_t *ki = c->keys, *ko = c->keys_alt, *vi = c->vals, *vo = c->vals_alt;
+        KernelTimer sort_timer(c, SMART_KT_BIN_SORT);
         for (int shift = 0; shift < bits; shift += RADIX_BITS) {
             k_radix_hist<<<(unsigned)ntiles, SORT_THREADS, 0, s>>>(ki, n, shift, ntiles, c->hist);
             st = scan_impl<uint32_t>(c, c->hist, (int64_t)RADIX * ntiles, hscan, (int64_t)RADIX * ntiles,
@@ -373,11 +377,15 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     st = scan_impl<int32_t>(c, counts, npix + 1, c->offsets, npix + 1, (int32_t *)c->scan_tmp, c->cap_scan * 2);
     if (st != SMART_OK) return st;
     if (n > 0) {
+        KernelTimer timer(c, SMART_KT_BIN_RECORDS);
         k_records<<<grid_for(n, 256), 256, 0, s>>>(N, c->keys, c->vals, n, ra, dec, e1, e2, w, c->ring_lat,
                                                    c->rec_geo, c->rec_shear, c->rec_radec);
         if ((st = check_cuda(c, cudaGetLastError(), "k_records")) != SMART_OK) return st;
     }
-    k_pixel_sums<<<grid_for(npix, 256), 256, 0, s>>>(c->offsets, npix, c->rec_shear, c->own_px, c->own_np);
+    {
+        KernelTimer timer(c, SMART_KT_BIN_PIXEL_SUMS);
+        k_pixel_sums<<<grid_for(npix, 256), 256, 0, s>>>(c->offsets, npix, c->rec_shear, c->own_px, c->own_np);
+    }
     if ((st = check_cuda(c, cudaGetLastError(), "k_pixel_sums")) != SMART_OK) return st;
     c->PX = c->own_px;
     c->NP = c->own_np;

@@ -91,6 +91,7 @@ extern "C" void smart_destroy(smart_ctx *c) {
                     c->d_status, c->d_fp64_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
 
@@ -217,4 +218,79 @@ extern "C" int64_t smart_last_fp64_decisions(smart_ctx *c) {
     cudaMemcpyAsync(&h, c->d_fp64_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
     cudaStreamSynchronize(c->stream);
     return (int64_t)h;
+}
+
+// ------------------------------------------------------------ kernel timing
+namespace smart {
+
+static cudaEvent_t timing_event(smart_ctx *c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+KernelTimer::KernelTimer(smart_ctx *c, int id) : c_(c), id_(id) {
+    if (!c_->timing) return;
+    start_ = timing_event(c_);
+    if (start_) cudaEventRecord(start_, c_->stream);
+}
+
+KernelTimer::~KernelTimer() {
+    if (!c_->timing || !start_) return;
+    cudaEvent_t stop = timing_event(c_);
+    if (!stop) return;
+    cudaEventRecord(stop, c_->stream);
+    c_->tlog[id_].emplace_back(start_, stop);
+}
+
+}  // namespace smart
+
+extern "C" smart_status smart_timing_enable(smart_ctx *c, int enable) {
+    if (!c) return SMART_E_ARG;
+    c->timing = enable != 0;
+    c->ev_used = 0;
+    for (auto &l : c->tlog) l.clear();
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_timing_read(smart_ctx *c, int kernel, int64_t *launches, double *total_ms,
+                                          double timeout_s) {
+    if (!c) return SMART_E_ARG;
+    if (kernel < 0 || kernel >= SMART_KT_COUNT || !launches || !total_ms)
+        return fail(c, SMART_E_ARG, "smart_timing_read: bad kernel id or null output");
+    double sum = 0.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (const auto &pr : c->tlog[kernel]) {
+        for (;;) {          // bounded wait for the stop event
+            const cudaError_t e = cudaEventQuery(pr.second);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) return check_cuda(c, e, "smart_timing_read");
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (timeout_s > 0 && dt > timeout_s) return fail(c, SMART_E_TIMEOUT, "smart_timing_read: deadline passed");
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        float ms = 0.f;
+        smart_status st = check_cuda(c, cudaEventElapsedTime(&ms, pr.first, pr.second), "cudaEventElapsedTime");
+        if (st != SMART_OK) return st;
+        sum += ms;
+    }
+    *launches = (int64_t)c->tlog[kernel].size();
+    *total_ms = sum;
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_get_general_targets(smart_ctx *c, int32_t *idx, int64_t cap, int64_t *n_gen) {
+    if (!c || !n_gen) return SMART_E_ARG;
+    if (c->gen_version != c->targets_version)
+        return fail(c, SMART_E_STATE, "smart_get_general_targets: no pixel map since the targets were set");
+    *n_gen = c->n_gen;
+    if (idx && c->n_gen > 0) {
+        if (cap < c->n_gen) return fail(c, SMART_E_ARG, "smart_get_general_targets: output too small");
+        return check_cuda(c, cudaMemcpyAsync(idx, c->gen_list, (size_t)c->n_gen * sizeof(int32_t),
+                                             cudaMemcpyDeviceToDevice, c->stream), "smart_get_general_targets");
+    }
+    return SMART_OK;
 }

@@ -10,6 +10,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/smart.h"
 
@@ -351,6 +353,10 @@ struct smart_ctx {
 
     // diagnostics
     unsigned long long *d_fp64_count = nullptr;
+    bool timing = false;                             // record events around each kernel launch
+    std::vector<cudaEvent_t> ev_pool;                // created on demand, reused after a reset
+    size_t ev_used = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tlog[SMART_KT_COUNT];
 };
 
 namespace smart {
@@ -376,5 +382,17 @@ smart_status build_tiles_log2(smart_ctx *ctx, int log2_slots, int64_t **tiles, i
 
 // context.cu
 smart_status ensure_own_binned_map(smart_ctx *ctx);
+
+// Brackets one kernel launch with events on the context stream while timing
+// is enabled (smart_timing_enable); does nothing otherwise.
+class KernelTimer {
+  public:
+    KernelTimer(smart_ctx *c, int id);
+    ~KernelTimer();
+  private:
+    smart_ctx *c_;
+    int id_;
+    cudaEvent_t start_ = nullptr;
+};
 
 }  // namespace smart

@@ -1,0 +1,58 @@
+"""Per-kernel timing record and the general-target query of the library."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_11181_b300 import api
+
+from _cases import binned_field_oracle, catalog, cap_targets
+
+pytestmark = pytest.mark.gpu
+
+
+def test_pixel_timing_and_general_targets(cuda_device):
+    # a cap reaching the polar rings: both pixel kernels run
+    nside = 256
+    b, foot = binned_field_oracle(21, nside, 30.0, 40.0, 12.0, mean_count=10.0)
+    tg = torch.from_numpy(np.nonzero(foot)[0].astype(np.int64)).to(cuda_device)
+    ctx = api.Context(nside, 30.0, "schirmer", nside_bin=nside)
+    ctx.set_targets(tg)
+    ctx.set_binned(*(x.to(cuda_device) for x in (b.G1, b.G2, b.W, b.S2, b.n)))
+    ctx.timing(True)
+    for _ in range(3):
+        ctx.map_pixel()
+    ctx.sync(60)
+    nt, mt = ctx.timing_read("pixel_toeplitz")
+    ng, mg = ctx.timing_read("pixel_general")
+    gen = ctx.general_targets()
+    assert 0 < gen.numel() < tg.numel()
+    assert nt == 3 and ng == 3 and mt > 0 and mg > 0
+    g = gen.cpu().numpy()
+    assert np.unique(g).size == g.size and g.min() >= 0 and g.max() < tg.numel()
+    # the general kernel takes whole output rings: every target of a listed ring is listed
+    ring_of = lambda p: np.searchsorted(np.cumsum([0] + [4 * min(i, nside, 4 * nside - i) for i in range(1, 4 * nside)]),
+                                        p, side="right")
+    rings = ring_of(tg.cpu().numpy())
+    listed = np.zeros(tg.numel(), bool)
+    listed[g] = True
+    for r in np.unique(rings[listed]):
+        assert listed[rings == r].all()
+    ctx.timing(False)
+    ctx.map_pixel()
+    ctx.sync(60)
+    assert ctx.timing_read("pixel_toeplitz")[0] == 0
+
+
+def test_bruteforce_and_binning_timing(cuda_device):
+    cat = catalog(22, 50_000, 120.0, -10.0, 3.0)
+    ctx = api.Context(128, 20.0, "poly", nside_bin=512)
+    ctx.set_targets(torch.from_numpy(cap_targets(128, 120.0, -10.0, 2.0)).to(cuda_device))
+    ctx.timing(True)
+    c = cat.to(cuda_device)
+    ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+    ctx.map_bruteforce()
+    ctx.sync(60)
+    for name in ("bin_keys", "bin_sort", "bin_records", "bin_pixel_sums", "galaxy", "galaxy_band",
+                 "galaxy_finalise"):
+        n, ms = ctx.timing_read(name)
+        assert n == 1 and ms >= 0.0, name
