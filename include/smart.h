@@ -6,10 +6,10 @@
  * centre theta_0, sum over the galaxies (brute force, Sect. 3.1 / 3.4) or
  * the binned shear pixels (pixel-based, Sect. 3.2) that lie within the
  * aperture radius theta_ap; rotate each shear into tangential and cross
- * components with the spherical position angle (Sect. 2.3, Eq. gammat),
+ * components with the spherical position angle (Sect. 2.3, Eq. 4),
  * weight by the filter Q, and normalise by the mean weight density inside
  * the aperture (the summed approach, Sect. 2.4).  Outputs per centre:
- * M_ap^E, M_ap^B (Eq. map), the noise variance (Eq. map_noise), the weight
+ * M_ap^E, M_ap^B (Eq. 7), the noise variance (Eq. 8), the weight
  * sum and the member count.
  *
  * Conventions shared by every call
@@ -67,9 +67,9 @@ typedef struct {
    NULL to skip that output). */
 typedef struct {
     double *sum_w;      /* f64 [n]: sum of weights in the aperture (Sect. 2.4)     */
-    float *map_e;       /* f32 [n]: M_ap^E, summed normalisation (Eq. map)          */
+    float *map_e;       /* f32 [n]: M_ap^E, summed normalisation (Eq. 7)          */
     float *map_b;       /* f32 [n]: M_ap^B                                          */
-    float *var;         /* f32 [n]: sigma_ap^2 (Eq. map_noise with weights)          */
+    float *var;         /* f32 [n]: sigma_ap^2 (Eq. 8 with weights)          */
     int64_t *count;     /* i64 [n]: galaxies in the aperture (brute force) or
                                     galaxies in the member pixels (pixel mode)    */
     int32_t *members;   /* i32 [n]: aperture members = (centre, point) pairs summed:

@@ -162,7 +162,7 @@ def query_disc(nside: int, r0, theta_ap: float, all_pixels: bool = False) -> np.
 
 
 # --------------------------------------------------------------------------
-# filters (Sect. 2, Eq. for Q from U; Schneider 1996; Schirmer et al. 2007)
+# filters (Sect. 2, Eq. 5; Schneider 1996; Schirmer et al. 2007)
 # --------------------------------------------------------------------------
 def filter_q(kind: int, x, xc: float = 0.15) -> np.ndarray:
     xs = np.atleast_1d(_f64(x))
@@ -230,7 +230,7 @@ def aperture_pixels_f32(centres, nside_bin, G1, G2, W, S2, n_p, kind, theta_ap, 
 
 
 def finalise(sums: dict, theta_ap: float) -> dict:
-    """Summed normalisation, Sect. 2.4 / Sect. 3.1 step 5, Eq. (map_noise)."""
+    """Summed normalisation, Sect. 2.4 / Sect. 3.1 step 5, Eq. 8."""
     SE, SB, SV, SW = (_f64(sums[k]) for k in ("SE", "SB", "SV", "SW"))
     n0 = SE.size
     ME, MB, VAR = (np.empty(n0) for _ in range(3))
@@ -272,7 +272,7 @@ def rms_rel(a, b) -> float:
 
 
 def epsilon_stats(m_x, m_ref):
-    """Sect. 4.1: eps_X = (M_X - M_ref) / sigma(M_ref); returns (mean, std)."""
+    """Sect. 5.1, Eq. 12: eps_X = (M_X - M_ref) / sigma(M_ref); returns (mean, std)."""
     m_x, m_ref = np.asarray(m_x, np.float64), np.asarray(m_ref, np.float64)
     eps = (m_x - m_ref) / np.std(m_ref)
     return float(np.mean(eps)), float(np.std(eps))

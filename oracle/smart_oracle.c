@@ -13,10 +13,10 @@
  * series below.
  *
  * Sections of the paper followed (by section / equation):
- *   Sect. 2, Eq. (map_gammat), Eq. (gammat)   tangential / cross shear
- *   Sect. 2, Eq. (Q from U)                    the Q filter
- *   Sect. 2.2, Eq. (map), Eq. (map_noise)      discrete sums, noise map
- *   Sect. 2.3, separation and position angle   spherical geometry
+ *   Sect. 2, Eq. 3, Eq. 4                      tangential / cross shear
+ *   Sect. 2, Eq. 5                             the Q filter
+ *   Sect. 2.2, Eq. 7, Eq. 8                    discrete sums, noise map
+ *   Sect. 2.3, Eq. 10, Eq. 11                  spherical geometry
  *   Sect. 2.4                                  summed normalisation
  *   Sect. 3 (HEALPix, Gorski et al. 2005)      RING pixelisation
  *   Sect. 3.1 steps 1-5                        brute force (sphS_pos)
@@ -292,7 +292,7 @@ double orc_filter_u_poly(double x)
 }
 
 /* ------------------------------------------------------------------ */
-/* One aperture term (Sect. 2.3 geometry, Eq. gammat).                  */
+/* One aperture term (Sect. 2.3 geometry, Eq. 4).                  */
 /* r0: unit vector of the aperture centre; p: unit vector of the point; */
 /* ehat, nhat: the point's local East and North unit vectors.           */
 /* Returns 1 when the point lies in the aperture (s^2 <= T).            */
@@ -604,7 +604,7 @@ void orc_aperture_pixels_f32(int64_t n0, const double *c, int64_t nside_bin,
  * Summed normalisation (Sect. 2.4 and Sect. 3.1 step 5): the mean density
  * inside the aperture is nbar = SW / A with A = 2 pi (1 - cos theta_ap), the
  * exact cap area.  M_E = SE / nbar, M_B = SB / nbar, sigma^2 = SV/(2 nbar^2)
- * (Eq. map_noise with weights).  Centres with SW = 0 get zeros.
+ * (Eq. 8 with weights).  Centres with SW = 0 get zeros.
  */
 void orc_finalise(int64_t n0, double theta_ap, const double *SE,
                   const double *SB, const double *SV, const double *SW,

@@ -284,3 +284,32 @@ def binned_field(centres: torch.Tensor, in_footprint: torch.Tensor, mean_count: 
         S2[ii] = (n * (2 * sigma_e ** 2 + g1 * g1 + g2 * g2)).float()
         cnt[ii] = n.to(torch.int32)
     return Binned(G1, G2, W, S2, cnt)
+
+
+# ---------------------------------------------------------------------------
+# random draws of the learned correction (passed to both sides as inputs)
+# ---------------------------------------------------------------------------
+MLP_LAYERS = ((64, 4), (64, 64), (1, 64))      # (out, in) of the three linear layers
+
+
+def mlp_init_params(seed: int) -> torch.Tensor:
+    """Initial parameter vector of the 4 -> 64 -> 64 -> 1 network (float32, CPU).
+
+    Layout W1 [64][4], b1 [64], W2 [64][64], b2 [64], w3 [64], b3; every
+    weight and bias of a layer uniform in +-1/sqrt(fan_in)."""
+    g = make_gen(seed)
+    parts_w, parts_b = [], []
+    for out, fan_in in MLP_LAYERS:
+        bound = 1.0 / math.sqrt(fan_in)
+        parts_w.append((torch.rand(out * fan_in, generator=g, dtype=torch.float64) * 2 - 1) * bound)
+        parts_b.append((torch.rand(out, generator=g, dtype=torch.float64) * 2 - 1) * bound)
+    return torch.cat([parts_w[0], parts_b[0], parts_w[1], parts_b[1], parts_w[2], parts_b[2]]).float()
+
+
+def minibatches(n: int, batch: int, epochs: int, seed: int, device="cpu"):
+    """Shuffled minibatch index lists (int32) for ``epochs`` passes over n samples."""
+    g = make_gen(seed, device)
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=g, device=device).to(torch.int32)
+        for s in range(0, n - batch + 1, batch):
+            yield perm[s:s + batch]
