@@ -273,6 +273,111 @@ smart_status smart_timing_read(smart_ctx *ctx, int kernel, int64_t *launches, do
  */
 smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_gen);
 
+/* ---- learned residual correction of the pixel-based map ------------ */
+
+/*
+ * The galaxy-level map (Sect. 3.1) and the pixel-based map (Sect. 3.2)
+ * differ because the second moves every galaxy to its pixel centre.  A small
+ * network predicts the per-pixel difference M_bf^E - M_pix^E from four
+ * features of the pixel-based map; the corrected map is written to a
+ * separate array and the plain map stays the fallback.  The paper prescribes
+ * no such network: features, architecture (4 -> 64 -> 64 -> 1, SiLU), loss
+ * (mean squared error on the standardised target) and optimiser (Adam,
+ * beta1 0.9, beta2 0.999, eps 1e-8) are this library's.
+ *
+ * Feature row of a target (float32, 4 values):
+ *   [0] M_pix^E   [1] sum of weights   [2] variance of the galaxy counts
+ *   n_p over the K bin pixels whose centre lies in the aperture,
+ *   sum n_p^2 / K - (sum n_p / K)^2   [3] z of the target pixel centre.
+ *
+ * Parameter vector (float32 master copy, SMART_MLP_NPARAMS values):
+ *   W1 [64][4], b1 [64], W2 [64][64], b2 [64], w3 [64], b3, W[out][in].
+ * SMART_MLP_BF16: the three weight matrices are used as their bfloat16
+ * roundings (biases float32); the 64 x 64 products run on bf16 tensor cores
+ * with float32 accumulation, the first hidden activation and the gradient at
+ * the second pre-activation are rounded to bfloat16 as tensor-core operands.
+ * SMART_MLP_FP32: every value and product in float32 (a checking mode).
+ *
+ * All array arguments are device pointers owned by the caller unless marked
+ * (host).  Calls run on the handle's stream; those marked "syncs" wait for
+ * it.  Errors: SMART_E_ARG bad argument, SMART_E_STATE no parameters yet,
+ * SMART_E_NOMEM, SMART_E_CUDA; smart_mlp_last_error tells which.
+ */
+#define SMART_MLP_FEATURES 4
+#define SMART_MLP_NPARAMS 4545
+
+typedef enum { SMART_MLP_BF16 = 0, SMART_MLP_FP32 = 1 } smart_mlp_precision;
+typedef struct smart_mlp smart_mlp;
+
+/*
+ * Features (and training targets) of ctx's targets.  pixel_map: the output
+ * of smart_map_pixel on ctx with map_e, sum_w, count and members set.
+ * brute_map (may be NULL): the output of smart_map_bruteforce for the same
+ * targets, map_e and sum_w set.  feat: out [n][4].  target: out [n],
+ * brute_map->map_e - pixel_map->map_e (needs brute_map; may be NULL).
+ * valid: out [n] (may be NULL), 1 where the pixel-based (and galaxy-level)
+ * weight sum is positive.  sum_n2: out [n] (may be NULL), sum of n_p^2 over
+ * the aperture's bin pixels.  Membership is that of the map kernels, so the
+ * count moments are exact integers.
+ */
+smart_status smart_mlp_features(smart_ctx *ctx, const smart_maps *pixel_map, const smart_maps *brute_map,
+                                float *feat, float *target, uint8_t *valid, int64_t *sum_n2);
+
+smart_status smart_mlp_create(int precision, void *cuda_stream, smart_mlp **out);
+void smart_mlp_destroy(smart_mlp *h);
+const char *smart_mlp_last_error(const smart_mlp *h);
+/* Bounded wait for the handle's stream (timeout_s <= 0: no deadline). */
+smart_status smart_mlp_sync(smart_mlp *h, double timeout_s);
+
+/* Load (host) float32 parameters; resets the Adam moments and step count. Syncs. */
+smart_status smart_mlp_set_params(smart_mlp *h, const float *params);
+/* Copy the float32 master parameters to params (host). Syncs. */
+smart_status smart_mlp_get_params(smart_mlp *h, float *params);
+
+/* Standardisation (host, 10 doubles): mean[4], sd[4] of the features, mean
+   and sd of the target; sd > 0. */
+smart_status smart_mlp_set_scaler(smart_mlp *h, const double *scaler);
+smart_status smart_mlp_get_scaler(smart_mlp *h, double *scaler);
+/* Fit the standardisation to rows `rows` (int32 [n]; NULL = rows 0..n-1) of
+   feat [.][4] and target: float64 mean and population sd, deterministic.  Syncs. */
+smart_status smart_mlp_fit_scaler(smart_mlp *h, const float *feat, const float *target, const int32_t *rows,
+                                  int64_t n);
+
+/*
+ * Gradient of the mean squared error over the minibatch idx[0..batch)
+ * (int32 rows of feat/target; NULL = rows 0..batch-1) with respect to the
+ * parameters.  grad_out (may be NULL): out [SMART_MLP_NPARAMS + 1]; the last
+ * value is the sum of squared errors over the batch.  Deterministic (fixed
+ * reduction order).
+ */
+smart_status smart_mlp_gradient(smart_mlp *h, const float *feat, const float *target, const int32_t *idx,
+                                int64_t batch, float *grad_out);
+/* Gradient as above, then one Adam step with learning rate lr; loss_out
+   (may be NULL): out [1], the batch's mean squared error. */
+smart_status smart_mlp_train_step(smart_mlp *h, const float *feat, const float *target, const int32_t *idx,
+                                  int64_t batch, float lr, float *loss_out);
+/* Adam steps taken since the parameters were set (host value). */
+int64_t smart_mlp_step(const smart_mlp *h);
+
+/*
+ * Corrected map: map_out[i] = map_plain[i] + sd_t * net(feat_i) + mean_t.
+ * Where a feature is not finite, the weight sum is not positive or a
+ * standardised feature lies beyond +-8, map_out[i] = map_plain[i] and
+ * n_fallback (may be NULL, device counter, not cleared here) is incremented.
+ * correction (may be NULL): out, the added value (0 at fallbacks).
+ * map_out must not alias map_plain.
+ */
+smart_status smart_mlp_infer(smart_mlp *h, const float *feat, const float *map_plain, int64_t n,
+                             float *map_out, float *correction, unsigned long long *n_fallback);
+
+/*
+ * Checkpoint: parameters, Adam moments, step count and standardisation in
+ * a flat byte buffer (host).  get_state with buf NULL only reports the size.
+ * set_state rejects a buffer of another size, version or precision.  Sync.
+ */
+smart_status smart_mlp_get_state(smart_mlp *h, void *buf, int64_t cap, int64_t *size);
+smart_status smart_mlp_set_state(smart_mlp *h, const void *buf, int64_t size);
+
 /* ---- catalogue sort without device allocation ---------------------- */
 
 /*

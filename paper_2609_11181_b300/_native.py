@@ -18,6 +18,11 @@ STATUS = {0: "SMART_OK", 1: "SMART_E_ARG", 2: "SMART_E_NOMEM", 3: "SMART_E_CUDA"
 KERNELS = {"pixel_toeplitz": 0, "pixel_general": 1, "galaxy": 2, "galaxy_band": 3, "galaxy_finalise": 4,
            "bin_keys": 5, "bin_sort": 6, "bin_records": 7, "bin_pixel_sums": 8}
 
+MLP_FEATURES = 4
+MLP_NPARAMS = 4545
+MLP_BF16 = 0
+MLP_FP32 = 1
+
 FILTER_POLY = 1
 FILTER_SCHIRMER = 2
 
@@ -60,6 +65,22 @@ SIGNATURES = {
     "smart_timing_enable": (_I32, [_VP, _I32]),
     "smart_timing_read": (_I32, [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), _D]),
     "smart_get_general_targets": (_I32, [_VP, _VP, _I64, ctypes.POINTER(_I64)]),
+    "smart_mlp_features": (_I32, [_VP, ctypes.POINTER(SmartMaps), ctypes.POINTER(SmartMaps), _VP, _VP, _VP, _VP]),
+    "smart_mlp_create": (_I32, [_I32, _VP, ctypes.POINTER(_VP)]),
+    "smart_mlp_destroy": (None, [_VP]),
+    "smart_mlp_last_error": (ctypes.c_char_p, [_VP]),
+    "smart_mlp_sync": (_I32, [_VP, _D]),
+    "smart_mlp_set_params": (_I32, [_VP, _VP]),
+    "smart_mlp_get_params": (_I32, [_VP, _VP]),
+    "smart_mlp_set_scaler": (_I32, [_VP, ctypes.POINTER(_D)]),
+    "smart_mlp_get_scaler": (_I32, [_VP, ctypes.POINTER(_D)]),
+    "smart_mlp_fit_scaler": (_I32, [_VP, _VP, _VP, _VP, _I64]),
+    "smart_mlp_gradient": (_I32, [_VP, _VP, _VP, _VP, _I64, _VP]),
+    "smart_mlp_train_step": (_I32, [_VP, _VP, _VP, _VP, _I64, ctypes.c_float, _VP]),
+    "smart_mlp_step": (_I64, [_VP]),
+    "smart_mlp_infer": (_I32, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "smart_mlp_get_state": (_I32, [_VP, _VP, _I64, ctypes.POINTER(_I64)]),
+    "smart_mlp_set_state": (_I32, [_VP, _VP, _I64]),
     "smart_sort_catalog_noalloc": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
 }
 

@@ -214,6 +214,23 @@ class Context:
                     "smart_get_catalog")
         return perm, pix, off
 
+    def mlp_features(self, pixel_out: dict, brute_out: dict | None = None, sum_n2: bool = False) -> dict:
+        """Features [M_pix^E, sum_w, var(n_p), z] of the targets from a pixel map of this context
+        (and, with a galaxy-level map of the same targets, the training target and validity)."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n = self.n_targets
+        _, pm = self._out(pixel_out)
+        feat = torch.empty((n, N.MLP_FEATURES), dtype=torch.float32, device=dev)
+        valid = torch.empty(n, dtype=torch.uint8, device=dev)
+        target = torch.empty(n, dtype=torch.float32, device=dev) if brute_out is not None else None
+        n2 = torch.empty(n, dtype=torch.int64, device=dev) if sum_n2 else None
+        bm = ctypes.byref(self._out(brute_out)[1]) if brute_out is not None else None
+        self._check(self._lib.smart_mlp_features(self._h, ctypes.byref(pm), bm, _ptr(feat, torch.float32, "feat"),
+                                                 _ptr(target, torch.float32, "target"),
+                                                 _ptr(valid, torch.uint8, "valid"), _ptr(n2, torch.int64, "n2")),
+                    "smart_mlp_features")
+        return dict(feat=feat, target=target, valid=valid, sum_n2=n2)
+
     def get_binned(self):
         dev = torch.device("cuda", torch.cuda.current_device())
         m = self.npix_bin
@@ -267,3 +284,117 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Residual:
+    """Learned residual correction of the pixel-based map (bf16 tensor-core
+    network, or the float32 checking mode)."""
+
+    def __init__(self, precision: str = "bf16", stream: torch.cuda.Stream | None = None):
+        self._lib = N.load()
+        prec = {"bf16": N.MLP_BF16, "fp32": N.MLP_FP32}[precision]
+        h = ctypes.c_void_p()
+        st = self._lib.smart_mlp_create(prec, _stream_handle(stream), ctypes.byref(h))
+        if st:
+            raise SmartError(st, "smart_mlp_create")
+        self._h = h
+        self.precision = precision
+
+    def _check(self, st: int, what: str):
+        if st:
+            msg = self._lib.smart_mlp_last_error(self._h)
+            raise SmartError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.smart_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- parameters and standardisation (host arrays)
+    def set_params(self, params: torch.Tensor):
+        p = params.detach().to("cpu", torch.float32).contiguous()
+        if p.numel() != N.MLP_NPARAMS:
+            raise ValueError(f"expected {N.MLP_NPARAMS} parameters")
+        self._check(self._lib.smart_mlp_set_params(self._h, ctypes.c_void_p(p.data_ptr())), "smart_mlp_set_params")
+
+    def get_params(self) -> torch.Tensor:
+        p = torch.empty(N.MLP_NPARAMS, dtype=torch.float32)
+        self._check(self._lib.smart_mlp_get_params(self._h, ctypes.c_void_p(p.data_ptr())), "smart_mlp_get_params")
+        return p
+
+    def set_scaler(self, scaler):
+        a = (ctypes.c_double * 10)(*[float(x) for x in scaler])
+        self._check(self._lib.smart_mlp_set_scaler(self._h, a), "smart_mlp_set_scaler")
+
+    def get_scaler(self) -> list:
+        a = (ctypes.c_double * 10)()
+        self._check(self._lib.smart_mlp_get_scaler(self._h, a), "smart_mlp_get_scaler")
+        return list(a)
+
+    def fit_scaler(self, feat: torch.Tensor, target: torch.Tensor, rows: torch.Tensor | None = None):
+        n = rows.numel() if rows is not None else target.numel()
+        self._check(self._lib.smart_mlp_fit_scaler(self._h, _ptr(feat, torch.float32, "feat"),
+                                                   _ptr(target, torch.float32, "target"),
+                                                   _ptr(rows, torch.int32, "rows"), n), "smart_mlp_fit_scaler")
+
+    # -- training
+    def gradient(self, feat, target, idx=None, batch: int | None = None) -> torch.Tensor:
+        """Gradient of the batch's mean squared error; the last entry is the sum of squared errors."""
+        n = idx.numel() if idx is not None else (batch if batch is not None else target.numel())
+        g = torch.empty(N.MLP_NPARAMS + 1, dtype=torch.float32, device=feat.device)
+        self._check(self._lib.smart_mlp_gradient(self._h, _ptr(feat, torch.float32, "feat"),
+                                                 _ptr(target, torch.float32, "target"), _ptr(idx, torch.int32, "idx"),
+                                                 n, _ptr(g, torch.float32, "grad")), "smart_mlp_gradient")
+        return g
+
+    def train_step(self, feat, target, idx, lr: float, loss_out: torch.Tensor | None = None):
+        self._check(self._lib.smart_mlp_train_step(self._h, _ptr(feat, torch.float32, "feat"),
+                                                   _ptr(target, torch.float32, "target"),
+                                                   _ptr(idx, torch.int32, "idx"), idx.numel(), float(lr),
+                                                   _ptr(loss_out, torch.float32, "loss")), "smart_mlp_train_step")
+
+    @property
+    def step(self) -> int:
+        return int(self._lib.smart_mlp_step(self._h))
+
+    def sync(self, timeout_s: float = 0.0):
+        self._check(self._lib.smart_mlp_sync(self._h, float(timeout_s)), "smart_mlp_sync")
+
+    # -- inference
+    def infer(self, feat: torch.Tensor, plain: torch.Tensor, out: torch.Tensor | None = None,
+              correction: torch.Tensor | None = None, n_fallback: torch.Tensor | None = None) -> torch.Tensor:
+        n = plain.numel()
+        if out is None:
+            out = torch.empty_like(plain)
+        self._check(self._lib.smart_mlp_infer(self._h, _ptr(feat, torch.float32, "feat", 4 * n),
+                                              _ptr(plain, torch.float32, "plain"), n,
+                                              _ptr(out, torch.float32, "out", n),
+                                              _ptr(correction, torch.float32, "correction", n),
+                                              _ptr(n_fallback, torch.int64, "n_fallback", 1)), "smart_mlp_infer")
+        return out
+
+    # -- checkpoint
+    def state(self) -> bytes:
+        size = ctypes.c_int64()
+        self._check(self._lib.smart_mlp_get_state(self._h, None, 0, ctypes.byref(size)), "smart_mlp_get_state")
+        buf = ctypes.create_string_buffer(size.value)
+        self._check(self._lib.smart_mlp_get_state(self._h, buf, size.value, ctypes.byref(size)), "smart_mlp_get_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._check(self._lib.smart_mlp_set_state(self._h, buf, len(blob)), "smart_mlp_set_state")
+
+    def save(self, path: str):
+        with open(path, "wb") as f:
+            f.write(self.state())
+
+    def load(self, path: str):
+        with open(path, "rb") as f:
+            self.load_state(f.read())

@@ -1,0 +1,246 @@
+"""GPU parity of the learned residual correction against the float64 oracle
+(oracle/mlp.py), and what the trained network gains over the plain
+pixel-based map on held-out maps.
+
+Bars: count moments bit-exact; features within float32 rounding; float32
+checking mode: gradients within 1e-5 (relative norm per parameter block) of
+the oracle; bf16 mode: within 1e-4 of the oracle that rounds the same two
+tensor-core operands to bf16, and within 1e-2 of the unrounded oracle;
+Adam step within float32 rounding; resume from a checkpoint bit-identical.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mlp as omlp
+from paper_2609_11181_b300 import api, synth, workloads
+
+from _cases import ARCMIN, binned_field_oracle, catalog, cap_targets, rms_rel
+
+pytestmark = pytest.mark.gpu
+
+BLOCKS = {"W1": (omlp.OFF_W1, omlp.OFF_B1), "b1": (omlp.OFF_B1, omlp.OFF_W2), "W2": (omlp.OFF_W2, omlp.OFF_B2),
+          "b2": (omlp.OFF_B2, omlp.OFF_W3), "w3": (omlp.OFF_W3, omlp.OFF_B3), "b3": (omlp.OFF_B3, omlp.NPARAMS)}
+
+
+def _block_errors(g, ref):
+    return {k: float(np.linalg.norm(g[a:b] - ref[a:b]) / max(np.linalg.norm(ref[a:b]), 1e-30))
+            for k, (a, b) in BLOCKS.items()}
+
+
+def _toy(seed, n=1000):
+    rng = np.random.default_rng(seed)
+    raw = np.stack([rng.normal(0.002, 0.01, n), rng.uniform(300, 600, n), rng.gamma(3.0, 8.0, n),
+                    rng.uniform(-0.9, 0.9, n)], axis=1)
+    tgt = 0.3 * raw[:, 0] - 1e-5 * raw[:, 1] + rng.normal(0, 0.004, n)
+    return raw.astype(np.float32), tgt.astype(np.float32)
+
+
+def _scaler(raw, tgt):
+    mu, sd, tmu, tsd = omlp.fit_scaler(raw, tgt)
+    return list(mu) + list(sd) + [tmu, tsd], mu, sd, tmu, tsd
+
+
+def test_features_match_oracle(cuda_device):
+    nside = 256
+    b, foot = binned_field_oracle(31, nside, 150.0, 20.0, 6.0, mean_count=12.0)
+    tg = np.nonzero(foot)[0].astype(np.int64)
+    ctx = api.Context(nside, 30.0, "schirmer", nside_bin=nside)
+    ctx.set_targets(torch.from_numpy(tg).to(cuda_device))
+    ctx.set_binned(*(x.to(cuda_device) for x in (b.G1, b.G2, b.W, b.S2, b.n)))
+    px = ctx.map_pixel()
+    f = ctx.mlp_features(px, sum_n2=True)
+    ctx.sync(60)
+    cv = oracle.pix2vec(nside, tg)
+    K, S1, S2 = omlp.disc_count_moments(nside, cv, b.n.long().numpy(), 30.0 * ARCMIN)
+    np.testing.assert_array_equal(px["members"].cpu().numpy(), K)
+    np.testing.assert_array_equal(px["count"].cpu().numpy(), S1)
+    np.testing.assert_array_equal(f["sum_n2"].cpu().numpy(), S2)
+    ref = oracle.map_pixels(cv, nside, b.G1.double().numpy(), b.G2.double().numpy(), b.W.double().numpy(),
+                            b.S2.double().numpy(), b.n.long().numpy(), 2, 30.0 * ARCMIN)
+    want = omlp.features(ref["ME"], ref["SW"], S1, K, S2, cv[:, 2])
+    got = f["feat"].cpu().numpy().astype(np.float64)
+    assert rms_rel(got[:, 0], want[:, 0]) <= 1e-4
+    np.testing.assert_allclose(got[:, 1], want[:, 1], rtol=1e-6)
+    np.testing.assert_allclose(got[:, 2], want[:, 2], rtol=1e-6, atol=1e-6)
+    np.testing.assert_array_equal(got[:, 3], want[:, 3].astype(np.float32))
+    assert int(f["valid"].sum()) == int((ref["SW"] > 0).sum())
+
+
+def test_training_targets_match_oracle(cuda_device):
+    cat = catalog(32, 40_000, 70.0, -35.0, 3.0, nhalo=4, w_range=(0.5, 1.5), clumped=True)
+    tg = cap_targets(512, 70.0, -35.0, 2.0)
+    ctx = api.Context(512, 12.0, "schirmer", nside_bin=512)
+    ctx.set_targets(torch.from_numpy(tg).to(cuda_device))
+    c = cat.to(cuda_device)
+    ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+    bf = ctx.map_bruteforce()
+    px = ctx.map_pixel()
+    f = ctx.mlp_features(px, bf)
+    ctx.sync(60)
+    cv = oracle.pix2vec(512, tg)
+    ra, dec = cat.ra_deg.numpy(), cat.dec_deg.numpy()
+    e1, e2, w = cat.e1.double().numpy(), cat.e2.double().numpy(), cat.w.double().numpy()
+    rbf = oracle.map_galaxies(cv, ra, dec, e1, e2, w, 2, 12.0 * ARCMIN)
+    bb = oracle.bin_catalog(512, ra, dec, e1, e2, w)
+    rpx = oracle.map_pixels(cv, 512, bb["G1"], bb["G2"], bb["W"], bb["S2"], bb["n"], 2, 12.0 * ARCMIN)
+    t_ref = rbf["ME"] - rpx["ME"]
+    t_got = f["target"].cpu().numpy().astype(np.float64)
+    scale = np.sqrt(np.mean(rbf["ME"] ** 2))
+    assert np.sqrt(np.mean((t_got - t_ref) ** 2)) <= 2e-4 * scale
+    np.testing.assert_array_equal(f["valid"].cpu().numpy().astype(bool), (rbf["SW"] > 0) & (rpx["SW"] > 0))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_gradient_matches_oracle(cuda_device, precision):
+    raw, tgt = _toy(33)
+    sc, mu, sd, tmu, tsd = _scaler(raw, tgt)
+    theta = synth.mlp_init_params(33)
+    idx = np.random.default_rng(34).choice(raw.shape[0], 777, replace=False).astype(np.int32)   # ragged last tile
+    net = api.Residual(precision)
+    net.set_params(theta)
+    net.set_scaler(sc)
+    g = net.gradient(torch.from_numpy(raw).to(cuda_device), torch.from_numpy(tgt).to(cuda_device),
+                     torch.from_numpy(idx).to(cuda_device)).cpu().double().numpy()
+    X = (raw[idx].astype(np.float64) - mu) / sd
+    t = (tgt[idx].astype(np.float64) - tmu) / tsd
+    th = theta.double().numpy()
+    if precision == "fp32":
+        L, ref = omlp.loss_and_grad(th, X, t, weights="fp32")
+        errs = _block_errors(g[:-1], ref)
+        assert max(errs.values()) <= 1e-5, errs
+    else:
+        L, ref = omlp.loss_and_grad(th, X, t, weights="bf16", act="bf16")
+        errs = _block_errors(g[:-1], ref)
+        assert max(errs.values()) <= 1e-4, errs
+        L2, ref2 = omlp.loss_and_grad(th, X, t, weights="bf16", act="exact")
+        errs2 = _block_errors(g[:-1], ref2)
+        assert max(errs2.values()) <= 1e-2, errs2
+    assert math.isclose(g[-1] / idx.size, L, rel_tol=1e-5)
+
+
+def test_adam_steps_match_oracle(cuda_device):
+    raw, tgt = _toy(35, 2048)
+    sc, mu, sd, tmu, tsd = _scaler(raw, tgt)
+    theta = synth.mlp_init_params(35)
+    net = api.Residual("fp32")
+    net.set_params(theta)
+    net.set_scaler(sc)
+    feat, target = torch.from_numpy(raw).to(cuda_device), torch.from_numpy(tgt).to(cuda_device)
+    batches = [b.to(cuda_device) for b in synth.minibatches(2048, 512, 1, seed=36)]
+    lr = 2e-3
+    losses = torch.zeros(len(batches), device=cuda_device)
+    for k, b in enumerate(batches):
+        net.train_step(feat, target, b, lr, losses[k:k + 1])
+    got = net.get_params().double().numpy()
+    X = (raw.astype(np.float64) - mu) / sd
+    t = (tgt.astype(np.float64) - tmu) / tsd
+    ref, _, _, ref_losses = omlp.train(theta.double().numpy(), X, t, [b.cpu().numpy() for b in batches], lr,
+                                       weights="fp32")
+    np.testing.assert_allclose(losses.cpu().numpy(), ref_losses, rtol=1e-5)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-3 * lr)
+    assert net.step == len(batches)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_inference_matches_oracle_and_falls_back(cuda_device, precision):
+    raw, tgt = _toy(37, 600)
+    sc, mu, sd, tmu, tsd = _scaler(raw, tgt)
+    raw[5, 1] = 0.0                   # no weight
+    raw[6, 0] = np.nan                # not finite
+    raw[7, 2] = 1e9                   # far outside the training range
+    plain = np.random.default_rng(38).normal(0, 0.01, 600).astype(np.float32)
+    theta = synth.mlp_init_params(37)
+    net = api.Residual(precision)
+    net.set_params(theta)
+    net.set_scaler(sc)
+    pl = torch.from_numpy(plain).to(cuda_device)
+    corr = torch.empty_like(pl)
+    nfb = torch.zeros(1, dtype=torch.int64, device=cuda_device)
+    out = net.infer(torch.from_numpy(raw).to(cuda_device), pl, correction=corr, n_fallback=nfb)
+    torch.cuda.synchronize()
+    assert torch.equal(pl.cpu(), torch.from_numpy(plain))          # plain map untouched
+    assert int(nfb.item()) == 3
+    o, c = out.cpu().numpy(), corr.cpu().numpy()
+    np.testing.assert_array_equal(o[[5, 6, 7]], plain[[5, 6, 7]])
+    np.testing.assert_array_equal(c[[5, 6, 7]], 0.0)
+    keep = np.setdiff1d(np.arange(600), [5, 6, 7])
+    X = (raw[keep].astype(np.float64) - mu) / sd
+    y, _ = omlp.forward(theta.double().numpy(), X, weights="fp32" if precision == "fp32" else "bf16",
+                        act="exact" if precision == "fp32" else "bf16")
+    want = y * tsd + tmu
+    np.testing.assert_allclose(c[keep], want, rtol=2e-5, atol=2e-5 * np.abs(want).max())
+    np.testing.assert_allclose(o[keep], plain[keep] + c[keep], rtol=1e-6, atol=1e-9)
+
+
+def test_checkpoint_resume_is_bit_identical(cuda_device, tmp_path):
+    raw, tgt = _toy(39, 4096)
+    sc, *_ = _scaler(raw, tgt)
+    feat, target = torch.from_numpy(raw).to(cuda_device), torch.from_numpy(tgt).to(cuda_device)
+    batches = [b.to(cuda_device) for b in synth.minibatches(4096, 256, 2, seed=40)]
+    a = api.Residual("bf16")
+    a.set_params(synth.mlp_init_params(39))
+    a.set_scaler(sc)
+    for b in batches[:10]:
+        a.train_step(feat, target, b, 1e-3)
+    path = str(tmp_path / "residual.ckpt")
+    a.save(path)
+    for b in batches[10:]:
+        a.train_step(feat, target, b, 1e-3)
+    pa = a.get_params()
+    r = api.Residual("bf16")
+    r.load(path)
+    assert r.step == 10 and r.get_scaler() == a.get_scaler()
+    for b in batches[10:]:
+        r.train_step(feat, target, b, 1e-3)
+    assert torch.equal(r.get_params(), pa)
+    with pytest.raises(api.SmartError):
+        api.Residual("fp32").load(path)          # saved in another precision
+
+
+def _learned_maps(dev, seed, area_deg2, n_gal):
+    rng = np.random.default_rng(seed)
+    ra0 = float(rng.uniform(0, 360))
+    dec0 = math.degrees(math.asin(rng.uniform(-0.6, 0.6)))
+    wl = workloads.galaxy_workload(dev, api.pix2vec, n_gal=n_gal, area_deg2=area_deg2, nside_bin=2048, nside_out=2048,
+                                   theta_ap=10.0, filt="schirmer", seed=seed, ra0=ra0, dec0=dec0)
+    ctx = api.Context(2048, 10.0, "schirmer", nside_bin=2048)
+    ctx.set_targets(wl.targets)
+    c = wl.cat
+    ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+    bf = ctx.map_bruteforce()
+    px = ctx.map_pixel()
+    f = ctx.mlp_features(px, bf)
+    ctx.sync(120)
+    keep = f["valid"].bool()
+    out = dict(feat=f["feat"][keep], target=f["target"][keep], plain=px["map_e"][keep], brute=bf["map_e"][keep])
+    ctx.close()
+    return out
+
+
+def test_trained_network_improves_on_plain_pixel_map(cuda_device):
+    """Learned correction on held-out maps: 24 training and 6 held-out 20 deg^2
+    caps at 18.5 gal/arcmin^2 (half clumped), NSIDE 2048, Schirmer 10'."""
+    n_gal = int(20 * 3600 * 18.5)
+    train = [_learned_maps(cuda_device, 5000 + s, 20.0, n_gal) for s in range(24)]
+    held = [_learned_maps(cuda_device, 6000 + s, 20.0, n_gal) for s in range(6)]
+    feat = torch.cat([d["feat"] for d in train])
+    target = torch.cat([d["target"] for d in train])
+    net = api.Residual("bf16")
+    net.set_params(synth.mlp_init_params(41))
+    net.fit_scaler(feat, target)
+    lr = 2e-3
+    for k, b in enumerate(synth.minibatches(target.numel(), 4096, 8, seed=42, device=cuda_device)):
+        net.train_step(feat, target, b, lr if k < 600 else lr / 4)
+    plain_err, corr_err = [], []
+    for d in held:
+        corr = net.infer(d["feat"], d["plain"])
+        b = d["brute"].double()
+        plain_err.append(float(((d["plain"].double() - b).pow(2).mean() / b.pow(2).mean()).sqrt()))
+        corr_err.append(float(((corr.double() - b).pow(2).mean() / b.pow(2).mean()).sqrt()))
+    p, q = float(np.mean(plain_err)), float(np.mean(corr_err))
+    print(f"held-out rms(M - M_bf)/rms(M_bf): plain {p:.4f}, corrected {q:.4f} ({100 * (1 - q / p):.1f}% lower)")
+    assert q < p
