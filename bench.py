@@ -546,6 +546,125 @@ def run_native_batch(args, world, rank):
     return res
 
 
+LEARNED = dict(area_deg2=300.0, n_gal=20_000_000, nside=2048, theta_ap=10.0, filt="schirmer", batch=8192,
+               epochs=4, lr=2e-3)
+
+
+def run_native_learned(args, world, rank):
+    """Learned residual correction: maps of seeded 300 deg^2 caps (2e7 galaxies,
+    half clumped) at NSIDE 2048, Schirmer 10'; the network is trained on the
+    training maps' brute-force minus pixel-based residuals and judged against
+    brute force on held-out maps."""
+    from paper_2609_11181_b300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    L = LEARNED
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(L["nside"], L["theta_ap"], L["filt"], nside_bin=L["nside"])
+    ev = lambda: torch.cuda.Event(enable_timing=True)   # noqa: E731
+    gen_s, t_bin, t_bf, t_px, t_feat, pairs_bf, pairs_px = 0.0, [], [], [], [], 0, 0
+    train, held = [], []
+    n_maps = args.train_maps + args.eval_maps
+    for k in range(n_maps):
+        rng = np.random.default_rng(9000 + k)
+        ra0 = float(rng.uniform(0, 360))
+        dec0 = math.degrees(math.asin(rng.uniform(-0.8, 0.8)))
+        t0 = time.perf_counter()
+        wl = workloads.galaxy_workload(dev, api.pix2vec, n_gal=L["n_gal"], area_deg2=L["area_deg2"],
+                                       nside_bin=L["nside"], nside_out=L["nside"], theta_ap=L["theta_ap"],
+                                       filt=L["filt"], seed=9000 + k, ra0=ra0, dec0=dec0)
+        torch.cuda.synchronize()
+        gen_s += time.perf_counter() - t0
+        e = [ev() for _ in range(5)]
+        ctx.set_targets(wl.targets)
+        c = wl.cat
+        e[0].record(stream)
+        ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+        e[1].record(stream)
+        bf = ctx.map_bruteforce()
+        e[2].record(stream)
+        px = ctx.map_pixel()
+        e[3].record(stream)
+        f = ctx.mlp_features(px, bf)
+        e[4].record(stream)
+        torch.cuda.synchronize()
+        t_bin.append(e[0].elapsed_time(e[1]))
+        t_bf.append(e[1].elapsed_time(e[2]))
+        t_px.append(e[2].elapsed_time(e[3]))
+        t_feat.append(e[3].elapsed_time(e[4]))
+        pairs_bf += int(bf["members"].long().sum())
+        pairs_px += int(px["members"].long().sum())
+        keep = f["valid"].bool()
+        d = dict(feat=f["feat"][keep].clone(), target=f["target"][keep].clone(), plain=px["map_e"][keep].clone(),
+                 brute=bf["map_e"][keep].clone())
+        (train if k < args.train_maps else held).append(d)
+        del wl, c, bf, px, f
+    feat = torch.cat([d["feat"] for d in train])
+    target = torch.cat([d["target"] for d in train])
+    net = api.Residual("bf16")
+    net.set_params(synth.mlp_init_params(2609))
+    net.fit_scaler(feat, target)
+    batches = list(synth.minibatches(target.numel(), L["batch"], L["epochs"], seed=2610, device=dev))
+    n_steps = len(batches)
+    torch.cuda.synchronize()
+    tr0, tr1 = ev(), ev()
+    tr0.record(stream)
+    for k, b in enumerate(batches):
+        net.train_step(feat, target, b, L["lr"] if k < 0.75 * n_steps else L["lr"] / 4)
+    tr1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = tr0.elapsed_time(tr1)
+    # held-out maps: corrected map (features + inference) against brute force
+    t_inf, err_plain, err_corr, eps_plain, eps_corr = [], [], [], [], []
+    nfb = torch.zeros(1, dtype=torch.int64, device=dev)
+    for d in held:
+        a, b = ev(), ev()
+        a.record(stream)
+        corr = net.infer(d["feat"], d["plain"], n_fallback=nfb)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_inf.append(a.elapsed_time(b))
+        ref = d["brute"].double()
+        rms = float(ref.pow(2).mean().sqrt())
+        sd = float(ref.std(unbiased=False))
+        for m, err, eps in ((d["plain"].double(), err_plain, eps_plain), (corr.double(), err_corr, eps_corr)):
+            diff = m - ref
+            err.append(float(diff.pow(2).mean().sqrt()) / rms)
+            eps.append((float(diff.mean()) / sd, float(diff.std(unbiased=False)) / sd))
+    n_held = sum(d["plain"].numel() for d in held)
+    ms_px = statistics.mean(t_px)
+    ms_learned = ms_px + statistics.mean(t_feat) + statistics.mean(t_inf)
+    pairs_px_map = pairs_px / n_maps
+    ctx.close()
+    return {"metric": METRIC, "value": round(pairs_px_map / (ms_learned * 1e-3) / 1e9, 3), "unit": "Gpair/s",
+            "n_gpus": world, "steps": len(held), "warmup": 0, "ms_per_step": round(ms_learned, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": "learned", "train_maps": args.train_maps, "eval_maps": args.eval_maps,
+                       "desc": f"{L['area_deg2']:.0f} deg^2 caps at seeded centres, {L['n_gal']} galaxies (half "
+                               f"clumped, w~U[0.5,1.5]), SIS field, NSIDE {L['nside']} bins and output, "
+                               f"{L['filt']} theta_ap={L['theta_ap']}'",
+                       "network": "4-64-64-1 SiLU, bf16 weights, f32 accumulation, Adam",
+                       "batch": L["batch"], "epochs": L["epochs"], "lr": L["lr"]},
+            "forms": {
+                "brute_force": {"ms_per_map": round(statistics.mean(t_bf), 3),
+                                "bin_ms_per_map": round(statistics.mean(t_bin), 3),
+                                "gpair_s": round(pairs_bf / n_maps / (statistics.mean(t_bf) * 1e-3) / 1e9, 3),
+                                "rms_err_vs_brute": 0.0},
+                "pixel_plain": {"ms_per_map": round(ms_px, 3), "rms_err_vs_brute": round(float(np.mean(err_plain)), 5),
+                                "eps_mean": round(float(np.mean([e[0] for e in eps_plain])), 5),
+                                "eps_std": round(float(np.mean([e[1] for e in eps_plain])), 5)},
+                "pixel_learned": {"ms_per_map": round(ms_learned, 3),
+                                  "features_ms": round(statistics.mean(t_feat), 3),
+                                  "infer_ms": round(statistics.mean(t_inf), 3),
+                                  "rms_err_vs_brute": round(float(np.mean(err_corr)), 5),
+                                  "eps_mean": round(float(np.mean([e[0] for e in eps_corr])), 5),
+                                  "eps_std": round(float(np.mean([e[1] for e in eps_corr])), 5),
+                                  "fallback_pixels": int(nfb.item()), "held_out_pixels": n_held}},
+            "training": {"samples": int(target.numel()), "steps": n_steps, "ms": round(train_ms, 1),
+                         "samples_per_s": round(n_steps * L["batch"] / (train_ms * 1e-3), 1)},
+            "input_gen_s": round(gen_s, 1)}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return None
@@ -582,7 +701,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="pixel4096",
-                    choices=sorted(PIXEL_WORKLOADS) + sorted(GALAXY_WORKLOADS) + ["batch64"])
+                    choices=sorted(PIXEL_WORKLOADS) + sorted(GALAXY_WORKLOADS) + ["batch64", "learned"])
+    ap.add_argument("--train-maps", type=int, default=200)
+    ap.add_argument("--eval-maps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -592,6 +713,8 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload == "batch64":
         res = run_native_batch(args, world, rank)
+    elif args.workload == "learned":
+        res = run_native_learned(args, world, rank)
     elif args.workload in GALAXY_WORKLOADS:
         res = run_native_galaxy(args, world, rank)
     else:

@@ -174,9 +174,11 @@ def sis_shear(ra_deg, dec_deg, halos: Halos, r_trunc: float, chunk: int = 1 << 2
     corners = torch.tensor([[a, b, c] for a in (0, 1) for b in (0, 1) for c in (0, 1)],
                            dtype=torch.long, device=dev)
     for s in range(0, n, chunk):
-        ra = ra_deg[s:s + chunk]
-        dec = dec_deg[s:s + chunk]
-        pv = radec_deg_to_vec(ra, dec)
+        ra = torch.deg2rad(ra_deg[s:s + chunk])
+        dec = torch.deg2rad(dec_deg[s:s + chunk])
+        m = ra.numel()
+        ca, sa, cd, sd = torch.cos(ra), torch.sin(ra), torch.cos(dec), torch.sin(dec)
+        pv = torch.stack([cd * ca, cd * sa, sd], -1)
         base = torch.floor((pv + 1.0) / L - 0.5).long() + 1
         cells = base[:, None, :] + corners[None, :, :]          # (m, 8, 3)
         ck = key(cells)
@@ -184,23 +186,32 @@ def sis_shear(ra_deg, dec_deg, halos: Halos, r_trunc: float, chunk: int = 1 << 2
         hit = uniq[pos] == ck.reshape(-1)
         cand = table[pos]                                       # (m*8, maxc)
         cand = torch.where(hit[:, None], cand, torch.full_like(cand, -1))
-        cand = cand.reshape(ra.numel(), 8 * maxc)
-        valid = cand >= 0
+        cand = cand.reshape(m, 8 * maxc)
         ci = cand.clamp(min=0)
-        cosd = (pv[:, None, :] * hv[ci]).sum(-1)
-        valid &= cosd >= cos_tr
-        theta = torch.acos(torch.clamp(cosd, -1.0, 1.0))
-        valid &= theta > 0
-        th_eff = torch.maximum(theta, hte[ci]) if inner_cut else torch.clamp(theta, min=1e-30)
-        gt = torch.where(valid, hte[ci] / (2.0 * th_eff), torch.zeros_like(theta))
-        a = torch.deg2rad(ra)[:, None]
-        d = torch.deg2rad(dec)[:, None]
-        da = ha[ci] - a
-        hdc = hd[ci]
-        b = torch.atan2(torch.sin(da) * torch.cos(hdc),
-                        torch.cos(d) * torch.sin(hdc) - torch.sin(d) * torch.cos(hdc) * torch.cos(da))
-        g1[s:s + chunk] = (gt * torch.cos(2 * b)).sum(-1)
-        g2[s:s + chunk] = (-gt * torch.sin(2 * b)).sum(-1)
+        cosd = pv[:, 0:1] * hv[ci, 0] + pv[:, 1:2] * hv[ci, 1] + pv[:, 2:3] * hv[ci, 2]
+        rows, cols = torch.nonzero((cand >= 0) & (cosd >= cos_tr), as_tuple=True)
+        hi = ci[rows, cols]
+        h = hv[hi]
+        # separation from the chord; bearing b of the halo from the point (from
+        # North through East) from its components along the local East and North
+        theta = 2.0 * torch.asin(torch.clamp(0.5 * torch.linalg.norm(h - pv[rows], dim=-1), max=1.0))
+        te = hte[hi]
+        th_eff = torch.maximum(theta, te) if inner_cut else torch.clamp(theta, min=1e-30)
+        gt = torch.where(theta > 0, te / (2.0 * th_eff), torch.zeros_like(theta))
+        a_c, a_s, d_c, d_s = ca[rows], sa[rows], cd[rows], sd[rows]
+        eh = -a_s * h[:, 0] + a_c * h[:, 1]                    # sin(b) * sin(theta)
+        nh = -d_s * (a_c * h[:, 0] + a_s * h[:, 1]) + d_c * h[:, 2]  # cos(b) * sin(theta)
+        q = eh * eh + nh * nh
+        qs = torch.where(q > 0, q, torch.ones_like(q))
+        c2b = torch.where(q > 0, (nh * nh - eh * eh) / qs, torch.ones_like(q))
+        s2b = torch.where(q > 0, 2.0 * eh * nh / qs, torch.zeros_like(q))
+        # back to one row per point (unique positions) and summed in a fixed order
+        t1 = torch.zeros((m, 8 * maxc), dtype=torch.float64, device=dev)
+        t2 = torch.zeros((m, 8 * maxc), dtype=torch.float64, device=dev)
+        t1[rows, cols] = gt * c2b
+        t2[rows, cols] = -gt * s2b
+        g1[s:s + chunk] = t1.sum(-1)
+        g2[s:s + chunk] = t2.sum(-1)
     return g1, g2
 
 
