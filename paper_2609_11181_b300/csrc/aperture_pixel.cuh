@@ -115,16 +115,27 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
         const int cnt = part == 0 ? n1 : len - n1;
+        if (cnt <= 0) continue;
         const int pbeg = part == 0 ? R.start + kk0 : R.start;
+        const int plast = pbeg + cnt - 1;
         float kf = (float)(part == 0 ? kl : kl + n1);
+        // the bin pixel's data is loaded one iteration ahead (the load of the
+        // last pixel is repeated, never past the run)
+        float4 gn = __ldg(a.PX + pbeg);
+        int nnext = __ldg(a.NP + pbeg);
 #pragma unroll 1
         for (int i = 0; i < cnt; ++i) {
+            const int p = pbeg + i;
+            const float4 g = gn;
+            const int np = nnext;
+            const int pn = min(p + 1, plast);
+            gn = __ldg(a.PX + pn);
+            nnext = __ldg(a.NP + pn);
             const float u = fmaf(kf, R.dphi, u0);
             kf += 1.0f;
             float sinu, h;
             sin_hav<MODE>(u, sinu, h);
             const float s2 = fmaf(R.B, h, R.A);
-            const int p = pbeg + i;
             if (s2 >= a.Tlo) {
                 if (s2 <= a.Thi) {
                     if (ndef == 0) {
@@ -146,12 +157,11 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             const float ss = -2.0f * x * y;
             const float Q = filter_Q<KIND>(a.f, qtab, s2);
             const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
-            const float4 g = __ldg(a.PX + p);
             pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
             pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
             pv = fmaf(Q * Q, g.z, pv);
             pw += g.w;
-            nn += __ldg(a.NP + p);
+            nn += np;
             nm += 1;
         }
     }
