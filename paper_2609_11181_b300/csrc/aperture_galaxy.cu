@@ -119,6 +119,67 @@ struct BandPair {
     int32_t entry;      // ring-pair entry of the target's output ring
 };
 
+// The galaxies of one ring pair's union window for the warp's targets: lanes
+// stride over the contiguous galaxy runs; each galaxy record serves every
+// target.  The per-target body has no branch on membership (non-members add
+// zeros), so the GT independent chains can interleave; guard-band pairs take
+// a rare branch to the float64 list.
+template <int KIND, bool SMALL>
+__device__ __forceinline__ void gal_segment(const MapArgs &a, const RingPair &Rp, const GalRing &R, int e, int lane,
+                                            int64_t tb, const bool (&on)[GT], const int (&Xi)[GT],
+                                            const float (&Xf)[GT], int lo, int len, float (&pe)[GT], float (&pb)[GT],
+                                            float (&pv)[GT], float (&pw)[GT], int (&nn)[GT]) {
+    const int n1 = min(len, Rp.nr - lo);
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+        const int pa = part == 0 ? lo : 0;
+        const int pn = part == 0 ? n1 : len - n1;
+        if (pn <= 0) continue;
+        const int g0 = __ldg(a.offsets + R.start + pa);
+        const int g1 = __ldg(a.offsets + R.start + pa + pn);
+#pragma unroll 1
+        for (int g = g0 + lane; g < g1; g += 32) {
+            const float4 geo = __ldg(a.geo + g);
+            const float4 sh = __ldg(a.shear + g);
+            const int kg = (int)__ldg(a.keys + g) - R.start;
+            float A, B, C, D, frg;
+            gal_setup(R, geo, A, B, C, D, frg);
+#pragma unroll
+            for (int r = 0; r < GT; ++r) {
+                const float u = gal_u(R, kg, frg, Xi[r], Xf[r]);
+                float sinu, h;
+                if (SMALL) sin_hav_small(u, sinu, h);
+                else sin_hav_wide(u, sinu, h);
+                const float s2 = fmaf(B, h, A);
+                const bool in = on[r] && s2 < a.Tlo;
+                if (on[r] && !(s2 < a.Tlo) && s2 <= a.Thi) {
+                    const unsigned long long slot = atomicAdd(a.band_count, 1ull);
+                    if (slot < (unsigned long long)a.band_cap) {
+                        BandPair bp;
+                        bp.target = tb + r;
+                        bp.galaxy = g;
+                        bp.entry = e;
+                        reinterpret_cast<BandPair *>(a.band)[slot] = bp;
+                    }
+                }
+                const float x = R.mrho0 * sinu;
+                const float y = fmaf(D, h, C);
+                const float xx = x * x;
+                const float sd2 = fmaf(y, y, xx);
+                const float cc = fmaf(y, y, -xx);
+                const float ss = -2.0f * x * y;
+                const float Q = filter_Q<KIND>(a.f, a.f.qtab, s2);
+                const float w = (in && sd2 > 1e-30f) ? __fdividef(Q, sd2) : 0.f;
+                pe[r] = fmaf(w, fmaf(sh.x, cc, sh.y * ss), pe[r]);
+                pb[r] = fmaf(w, fmaf(sh.y, cc, -sh.x * ss), pb[r]);
+                pv[r] = fmaf(in ? Q * Q : 0.f, sh.w, pv[r]);
+                pw[r] += in ? sh.z : 0.f;
+                nn[r] += in ? 1 : 0;
+            }
+        }
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
     const int lane = threadIdx.x & 31;
@@ -179,58 +240,8 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
         int lo = ulo % Rp.nr;
         if (lo < 0) lo += Rp.nr;
         const int len = uhi - ulo + 1;
-        const int n1 = min(len, Rp.nr - lo);
-#pragma unroll 1
-        for (int part = 0; part < 2; ++part) {
-            const int pa = part == 0 ? lo : 0;
-            const int pn = part == 0 ? n1 : len - n1;
-            if (pn <= 0) continue;
-            const int g0 = __ldg(a.offsets + R.start + pa);
-            const int g1 = __ldg(a.offsets + R.start + pa + pn);
-#pragma unroll 1
-            for (int g = g0 + lane; g < g1; g += 32) {
-                const float4 geo = __ldg(a.geo + g);
-                const float4 sh = __ldg(a.shear + g);
-                const int kg = (int)__ldg(a.keys + g) - R.start;
-                float A, B, C, D, frg;
-                gal_setup(R, geo, A, B, C, D, frg);
-#pragma unroll
-                for (int r = 0; r < GT; ++r) {
-                    if (!on[r]) continue;
-                    const float u = gal_u(R, kg, frg, Xi[r], Xf[r]);
-                    float sinu, h;
-                    if (R.small) sin_hav_small(u, sinu, h);
-                    else sin_hav_wide(u, sinu, h);
-                    const float s2 = fmaf(B, h, A);
-                    if (s2 >= a.Tlo) {
-                        if (s2 <= a.Thi) {
-                            const unsigned long long slot = atomicAdd(a.band_count, 1ull);
-                            if (slot < (unsigned long long)a.band_cap) {
-                                BandPair bp;
-                                bp.target = tb + r;
-                                bp.galaxy = g;
-                                bp.entry = e;
-                                reinterpret_cast<BandPair *>(a.band)[slot] = bp;
-                            }
-                        }
-                        continue;
-                    }
-                    const float x = R.mrho0 * sinu;
-                    const float y = fmaf(D, h, C);
-                    const float xx = x * x;
-                    const float sd2 = fmaf(y, y, xx);
-                    const float cc = fmaf(y, y, -xx);
-                    const float ss = -2.0f * x * y;
-                    const float Q = filter_Q<KIND>(a.f, a.f.qtab, s2);
-                    const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
-                    pe[r] = fmaf(w, fmaf(sh.x, cc, sh.y * ss), pe[r]);
-                    pb[r] = fmaf(w, fmaf(sh.y, cc, -sh.x * ss), pb[r]);
-                    pv[r] = fmaf(Q * Q, sh.w, pv[r]);
-                    pw[r] += sh.z;
-                    nn[r] += 1;
-                }
-            }
-        }
+        if (R.small) gal_segment<KIND, true>(a, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn);
+        else gal_segment<KIND, false>(a, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn);
 #pragma unroll
         for (int r = 0; r < GT; ++r) {
             kahan_add(SE[r], cSE[r], pe[r]);

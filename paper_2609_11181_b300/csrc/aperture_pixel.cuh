@@ -123,7 +123,9 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
         // last pixel is repeated, never past the run)
         float4 gn = __ldg(a.PX + pbeg);
         int nnext = __ldg(a.NP + pbeg);
-#pragma unroll 1
+        // branch-free body (non-members add zeros), so that consecutive pairs
+        // can interleave; guard-band pairs take the rare branch
+#pragma unroll 2
         for (int i = 0; i < cnt; ++i) {
             const int p = pbeg + i;
             const float4 g = gn;
@@ -136,18 +138,16 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             float sinu, h;
             sin_hav<MODE>(u, sinu, h);
             const float s2 = fmaf(R.B, h, R.A);
-            if (s2 >= a.Tlo) {
-                if (s2 <= a.Thi) {
-                    if (ndef == 0) {
-                        def0 = p;
-                        ud0 = u;
-                    } else {
-                        def1 = p;
-                        ud1 = u;
-                    }
-                    ++ndef;
+            const bool in = s2 < a.Tlo;
+            if (!in && s2 <= a.Thi) {
+                if (ndef == 0) {
+                    def0 = p;
+                    ud0 = u;
+                } else {
+                    def1 = p;
+                    ud1 = u;
                 }
-                continue;
+                ++ndef;
             }
             const float x = R.mrho0 * sinu;
             const float y = fmaf(R.D, h, R.C);
@@ -156,13 +156,13 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             const float cc = fmaf(y, y, -xx);
             const float ss = -2.0f * x * y;
             const float Q = filter_Q<KIND>(a.f, qtab, s2);
-            const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
+            const float w = (in && sd2 > 1e-30f) ? __fdividef(Q, sd2) : 0.f;
             pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
             pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
-            pv = fmaf(Q * Q, g.z, pv);
-            pw += g.w;
-            nn += np;
-            nm += 1;
+            pv = fmaf(in ? Q * Q : 0.f, g.z, pv);
+            pw += in ? g.w : 0.f;
+            nn += in ? np : 0;
+            nm += in ? 1 : 0;
         }
     }
     if (ndef > 2) {
