@@ -250,16 +250,7 @@ def cpu_baseline_pixel(wl, G, budget_s=15.0, seed=0):
                       f"{dt:.1f} s"}, pairs, dt, m
 
 
-PIXEL_WORKLOADS = {
-    # the headline configuration
-    "pixel4096": dict(nside=4096, area_deg2=15000.0, theta_ap=10.0, filt="schirmer"),
-    # a small case of the same kernels for profiling: 3,000 deg^2 cap at dec 60
-    # (polar and equatorial rings), NSIDE 2048, theta_ap = 20' (about as many
-    # pixels per aperture as NSIDE 4096 at 10'); 1 GB of full-sky arrays
-    "pixel2048": dict(nside=2048, area_deg2=3000.0, theta_ap=20.0, filt="schirmer", dec0=60.0),
-    # the same at the equator (Toeplitz kernel only)
-    "pixel2048eq": dict(nside=2048, area_deg2=3000.0, theta_ap=20.0, filt="schirmer", dec0=0.0),
-}
+PIXEL_WORKLOADS = workloads.PIXEL_WORKLOADS
 
 
 def run_native_pixel(args, world, rank):
@@ -378,15 +369,7 @@ def run_native_pixel(args, world, rank):
     return res
 
 
-GALAXY_WORKLOADS = {
-    # 5e7 clustered galaxies on a 1,000 deg^2 cap, sorted into NSIDE 4096,
-    # output NSIDE 2048, polynomial filter, 15'
-    "brute2048": dict(n_gal=50_000_000, area_deg2=1000.0, nside_bin=4096, nside_out=2048, theta_ap=15.0,
-                      filt="poly"),
-    # a small case of the same kernels for profiling
-    "brute_small": dict(n_gal=4_000_000, area_deg2=100.0, nside_bin=4096, nside_out=2048, theta_ap=15.0,
-                        filt="poly"),
-}
+GALAXY_WORKLOADS = workloads.GALAXY_WORKLOADS
 # float32 flops per member pair of the brute-force kernel (source count, FMA = 2):
 # offsets 2, latitude series 10, azimuth series 9, chord 3, direction + 2psi 10,
 # filter 8, weight 1, E/B 10, variance + weight 4

@@ -115,3 +115,26 @@ def c1_workload(device, centres_fn, seed=101) -> GalaxyWorkload:
     targets = torch.nonzero(_cap_mask(v, 0.0, 0.0, radius), as_tuple=False).flatten().to(torch.int64)
     return GalaxyWorkload(256, 1024, 60.0, "poly", targets, cat, 5,
                           "10 deg cap; 2e5 uniform galaxies; 5 SIS; output NSIDE 256; poly 60'")
+
+
+# the benchmark configurations (keyword arguments of the builders above)
+PIXEL_WORKLOADS = {
+    # the headline configuration
+    "pixel4096": dict(nside=4096, area_deg2=15000.0, theta_ap=10.0, filt="schirmer"),
+    # a small case of the same kernels for profiling: 3,000 deg^2 cap at dec 60
+    # (polar and equatorial rings), NSIDE 2048, theta_ap = 20' (about as many
+    # pixels per aperture as NSIDE 4096 at 10'); 1 GB of full-sky arrays
+    "pixel2048": dict(nside=2048, area_deg2=3000.0, theta_ap=20.0, filt="schirmer", dec0=60.0),
+    # the same at the equator (Toeplitz kernel only)
+    "pixel2048eq": dict(nside=2048, area_deg2=3000.0, theta_ap=20.0, filt="schirmer", dec0=0.0),
+}
+
+GALAXY_WORKLOADS = {
+    # 5e7 clustered galaxies on a 1,000 deg^2 cap, sorted into NSIDE 4096,
+    # output NSIDE 2048, polynomial filter, 15'
+    "brute2048": dict(n_gal=50_000_000, area_deg2=1000.0, nside_bin=4096, nside_out=2048, theta_ap=15.0,
+                      filt="poly"),
+    # a small case of the same kernels for profiling
+    "brute_small": dict(n_gal=4_000_000, area_deg2=100.0, nside_bin=4096, nside_out=2048, theta_ap=15.0,
+                        filt="poly"),
+}
