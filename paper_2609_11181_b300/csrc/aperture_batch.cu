@@ -47,15 +47,25 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_batched(const MapArgs *__restri
     }
 }
 
-// the general targets of every map: one thread per (map, target) entry
+// the general targets of every map: one thread per (map, target) entry.
+// The list runs map by map, so the filter table of the block's first map is
+// staged in shared memory; entries of another map read theirs from global.
 template <int KIND>
-__global__ void __launch_bounds__(128, 6) k_pixel_batched_general(const MapArgs *__restrict__ maps,
+__global__ void __launch_bounds__(128, 5) k_pixel_batched_general(const MapArgs *__restrict__ maps,
                                                                    const int2 *__restrict__ list, int64_t n) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x;
+    const int m0 = list[i0].x;
+    if (KIND != SMART_FILTER_POLY) {
+        const float4 *src = maps[m0].f.qtab;
+        for (int k = threadIdx.x; k < QTAB_BINS; k += blockDim.x) qtab[k] = src[k];
+        __syncthreads();
+    }
+    const int64_t i = i0 + threadIdx.x;
     if (i >= n) return;
     const int2 e = list[i];
     const MapArgs &a = maps[e.x];
-    general_target<KIND>(a, e.y, a.f.qtab);
+    general_target<KIND>(a, e.y, e.x == m0 ? qtab : a.f.qtab);
 }
 
 __global__ void k_tiles_wanted(const MapArgs a, unsigned char *__restrict__ want) {
@@ -78,6 +88,8 @@ struct smart_batch {
     int64_t n_gen = 0;
     int *d_work = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;     // the general kernel runs here, beside the persistent kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool own_stream = false;
@@ -110,6 +122,23 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
     if (cudaMemsetAsync(b->d_work, 0, sizeof(int), b->stream) != cudaSuccess)
         return bfail(b, SMART_E_CUDA, "work counter reset failed");
     const int sms = b->ctxs[0]->num_sms;
+    // the general targets on the side stream, concurrent with the persistent
+    // kernel (fork after the count prefixes, join before the batch ends): the
+    // general blocks fill the SMs the persistent kernel's tail leaves idle
+    const bool fork = b->n_gen > 0 && b->n_items > 0;
+    if (fork) {
+        if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->side, b->ev_fork, 0) != cudaSuccess)
+            return bfail(b, SMART_E_CUDA, "fork of the general launch failed");
+    }
+    if (b->n_gen > 0) {
+        cudaStream_t gs = fork ? b->side : b->stream;
+        const unsigned grid = (unsigned)((b->n_gen + 127) / 128);
+        if (b->kind == SMART_FILTER_POLY)
+            k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen);
+        else
+            k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen);
+    }
     if (b->n_items > 0) {
         const unsigned grid = (unsigned)std::min<int64_t>(b->n_items, (int64_t)sms * ctas_per_sm);
         const BatchItem *items = b->d_items + (order == 0 ? 0 : b->n_items);
@@ -118,12 +147,10 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
         else
             k_pixel_batched<SMART_FILTER_SCHIRMER><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
     }
-    if (b->n_gen > 0) {
-        const unsigned grid = (unsigned)((b->n_gen + 127) / 128);
-        if (b->kind == SMART_FILTER_POLY)
-            k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, b->stream>>>(b->d_maps, b->d_gen, b->n_gen);
-        else
-            k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, b->stream>>>(b->d_maps, b->d_gen, b->n_gen);
+    if (fork) {
+        if (cudaEventRecord(b->ev_join, b->side) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->ev_join, 0) != cudaSuccess)
+            return bfail(b, SMART_E_CUDA, "join of the general launch failed");
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(b, SMART_E_CUDA, std::string("k_pixel_batched: ") + cudaGetErrorString(e));
@@ -146,6 +173,12 @@ extern "C" void smart_batch_destroy(smart_batch *b) {
     if (b->d_gen) cudaFree(b->d_gen);
     if (b->d_work) cudaFree(b->d_work);
     if (b->own_stream) cudaStreamDestroy(b->stream);
+    if (b->side) {
+        cudaStreamSynchronize(b->side);
+        cudaStreamDestroy(b->side);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     delete b;
 }
 
@@ -166,6 +199,13 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
             return SMART_E_CUDA;
         }
         b->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        bfail(b, SMART_E_CUDA, "side stream or events could not be created");
+        smart_batch_destroy(b);
+        return SMART_E_CUDA;
     }
     b->kind = ctxs[0] ? ctxs[0]->filter_kind : 0;
     for (int m = 0; m < n_maps; ++m) {

@@ -104,6 +104,30 @@ struct Smem<false> {
     float b3;
 };
 
+// forward-only image (inference): no transposes, no first pre-activation
+template <bool TC>
+struct SmemInf;
+
+template <>
+struct SmemInf<true> {
+    __nv_bfloat16 W2[H * LDH];
+    __nv_bfloat16 H1[S * LDH];
+    float A2[S * LDF];
+    float W1[H * F], b1[H], b2[H], w3[H];
+    float X[S * F], T[S], DY[S], M[S];
+    float b3;
+};
+
+template <>
+struct SmemInf<false> {
+    float W2[H * H];
+    float H1[S * H];
+    float A2[S * LDF];
+    float W1[H * F], b1[H], b2[H], w3[H];
+    float X[S * F], T[S], DY[S], M[S];
+    float b3;
+};
+
 __device__ __forceinline__ float sigmoidf_(float a) { return 1.0f / (1.0f + __expf(-a)); }
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
@@ -133,8 +157,8 @@ __device__ __forceinline__ void load_b(uint32_t &b0, uint32_t &b1, const __nv_bf
     b1 = ld32(Bt + (n0 + g) * ld + k0 + 8 + 2 * tg);
 }
 
-template <bool TC>
-__device__ void load_weights(Smem<TC> &s, const float *theta, const __nv_bfloat16 *wb) {
+template <bool TC, bool TRAIN = true, typename SM = Smem<TC>>
+__device__ void load_weights(SM &s, const float *theta, const __nv_bfloat16 *wb) {
     for (int i = threadIdx.x; i < H * F; i += NTH) s.W1[i] = TC ? __bfloat162float(wb[OFF_W1 + i]) : theta[OFF_W1 + i];
     for (int i = threadIdx.x; i < H; i += NTH) {
         s.b1[i] = theta[OFF_B1 + i];
@@ -147,7 +171,7 @@ __device__ void load_weights(Smem<TC> &s, const float *theta, const __nv_bfloat1
             const int n = i / H, k = i % H;
             const __nv_bfloat16 w = wb[OFF_W2 + i];
             s.W2[n * LDH + k] = w;
-            s.W2T[k * LDH + n] = w;
+            if constexpr (TRAIN) s.W2T[k * LDH + n] = w;
         } else {
             s.W2[i] = theta[OFF_W2 + i];
         }
@@ -158,8 +182,8 @@ __device__ void load_weights(Smem<TC> &s, const float *theta, const __nv_bfloat1
 // `count` get mask 0.  in_range (optional) marks the samples
 // whose raw features are finite, whose weight sum is positive and whose
 // standardised features lie within +-XMAX.
-template <bool TC>
-__device__ void load_samples(Smem<TC> &s, const float *feat, const float *target, const int32_t *idx, int64_t base,
+template <bool TC, typename SM = Smem<TC>>
+__device__ void load_samples(SM &s, const float *feat, const float *target, const int32_t *idx, int64_t base,
                              int64_t count, const Scaler &sc, bool *in_range) {
     for (int r = threadIdx.x; r < S; r += NTH) {
         const int64_t q = base + r;
@@ -185,19 +209,19 @@ __device__ void load_samples(Smem<TC> &s, const float *feat, const float *target
 }
 
 // layer 1 and the 64 x 64 layer: A1, H1, A2 (pre-activation incl. bias)
-template <bool TC>
-__device__ void forward_tile(Smem<TC> &s) {
+template <bool TC, bool TRAIN = true, typename SM = Smem<TC>>
+__device__ void forward_tile(SM &s) {
     for (int e = threadIdx.x; e < S * H; e += NTH) {
         const int r = e / H, n = e % H;
         float a = s.b1[n];
 #pragma unroll
         for (int f = 0; f < F; ++f) a = fmaf(s.W1[n * F + f], s.X[r * F + f], a);
-        s.A1[r * LDF + n] = a;
+        if constexpr (TRAIN) s.A1[r * LDF + n] = a;
         const float h = a * sigmoidf_(a);
         if constexpr (TC) {
             const __nv_bfloat16 hb = __float2bfloat16_rn(h);
             s.H1[r * LDH + n] = hb;
-            s.H1T[n * LDT + r] = hb;
+            if constexpr (TRAIN) s.H1T[n * LDT + r] = hb;
         } else {
             s.H1[r * H + n] = h;
         }
@@ -440,26 +464,36 @@ struct InferArgs {
     unsigned long long *n_fallback;
 };
 
+// persistent: each CTA loads the weights once and walks tiles of S samples;
+// the output layer uses two threads per sample (32 columns each)
 template <bool TC>
-__global__ void __launch_bounds__(NTH, 1) k_mlp_infer(const InferArgs a) {
+__global__ void __launch_bounds__(NTH) k_mlp_infer(const InferArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<TC> &s = *reinterpret_cast<Smem<TC> *>(smem_raw);
+    SmemInf<TC> &s = *reinterpret_cast<SmemInf<TC> *>(smem_raw);
     __shared__ bool in_range[S];
-    load_weights<TC>(s, a.theta, a.wb);
-    load_samples<TC>(s, a.feat, nullptr, nullptr, (int64_t)blockIdx.x * S, a.n, a.sc, in_range);
-    __syncthreads();
-    forward_tile<TC>(s);
-    const int r = threadIdx.x;
-    if (r < S) {
-        const int64_t q = (int64_t)blockIdx.x * S + r;
-        if (q < a.n) {
+    load_weights<TC, false>(s, a.theta, a.wb);
+    const int64_t ntiles = (a.n + S - 1) / S;
+    const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        load_samples<TC>(s, a.feat, nullptr, nullptr, tile * S, a.n, a.sc, in_range);
+        __syncthreads();
+        forward_tile<TC, false>(s);
+        float y = 0.f;
+        for (int n = half * (H / 2); n < (half + 1) * (H / 2); ++n) {
+            const float a2 = s.A2[r * LDF + n];
+            y = fmaf(s.w3[n], a2 * sigmoidf_(a2), y);
+        }
+        y += __shfl_xor_sync(0xffffffffu, y, 1);
+        const int64_t q = tile * S + r;
+        if (half == 0 && q < a.n) {
             const float plain = a.plain[q];
             float c = 0.f;
-            if (in_range[r]) c = fmaf(head<TC>(s, r), a.sc.t_sd, a.sc.t_mu);
+            if (in_range[r]) c = fmaf(y + s.b3, a.sc.t_sd, a.sc.t_mu);
             else if (a.n_fallback) atomicAdd(a.n_fallback, 1ull);
             a.out[q] = plain + c;
             if (a.corr) a.corr[q] = c;
         }
+        __syncthreads();       // the next tile overwrites the activations
     }
 }
 
@@ -834,20 +868,22 @@ extern "C" smart_status smart_mlp_infer(smart_mlp *h, const float *feat, const f
     a.out = map_out;
     a.corr = correction;
     a.n_fallback = n_fallback;
-    const unsigned blocks = (unsigned)((n + S - 1) / S);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (n + S - 1) / S;
     smart_status st;
     if (h->precision == SMART_MLP_BF16) {
-        const size_t smem = sizeof(Smem<true>);
+        const size_t smem = sizeof(SmemInf<true>);
         st = mcheck(h, cudaFuncSetAttribute(k_mlp_infer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                     "smem attribute");
         if (st != SMART_OK) return st;
-        k_mlp_infer<true><<<blocks, NTH, smem, h->stream>>>(a);
+        k_mlp_infer<true><<<(unsigned)std::min<int64_t>(ntiles, (int64_t)sms * 3), NTH, smem, h->stream>>>(a);
     } else {
-        const size_t smem = sizeof(Smem<false>);
+        const size_t smem = sizeof(SmemInf<false>);
         st = mcheck(h, cudaFuncSetAttribute(k_mlp_infer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                     "smem attribute");
         if (st != SMART_OK) return st;
-        k_mlp_infer<false><<<blocks, NTH, smem, h->stream>>>(a);
+        k_mlp_infer<false><<<(unsigned)std::min<int64_t>(ntiles, (int64_t)sms * 2), NTH, smem, h->stream>>>(a);
     }
     return mcheck(h, cudaGetLastError(), "k_mlp_infer");
 }

@@ -147,12 +147,13 @@ def test_adam_steps_match_oracle(cuda_device):
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_inference_matches_oracle_and_falls_back(cuda_device, precision):
-    raw, tgt = _toy(37, 600)
+    n = 40_000                        # more tiles than SMs: the persistent loop takes several
+    raw, tgt = _toy(37, n)
     sc, mu, sd, tmu, tsd = _scaler(raw, tgt)
     raw[5, 1] = 0.0                   # no weight
     raw[6, 0] = np.nan                # not finite
     raw[7, 2] = 1e9                   # far outside the training range
-    plain = np.random.default_rng(38).normal(0, 0.01, 600).astype(np.float32)
+    plain = np.random.default_rng(38).normal(0, 0.01, n).astype(np.float32)
     theta = synth.mlp_init_params(37)
     net = api.Residual(precision)
     net.set_params(theta)
@@ -163,16 +164,28 @@ def test_inference_matches_oracle_and_falls_back(cuda_device, precision):
     out = net.infer(torch.from_numpy(raw).to(cuda_device), pl, correction=corr, n_fallback=nfb)
     torch.cuda.synchronize()
     assert torch.equal(pl.cpu(), torch.from_numpy(plain))          # plain map untouched
-    assert int(nfb.item()) == 3
+    # fallbacks: the three planted rows and any row of the heavy-tailed toy
+    # features beyond 8 standard deviations
+    with np.errstate(invalid="ignore"):
+        z = (raw.astype(np.float64) - mu) / sd
+        fb = ~np.isfinite(raw).all(axis=1) | (raw[:, 1] <= 0) | (np.abs(z) > 8.0).any(axis=1)
+    assert fb[[5, 6, 7]].all()
+    assert int(nfb.item()) == int(fb.sum())
     o, c = out.cpu().numpy(), corr.cpu().numpy()
-    np.testing.assert_array_equal(o[[5, 6, 7]], plain[[5, 6, 7]])
-    np.testing.assert_array_equal(c[[5, 6, 7]], 0.0)
-    keep = np.setdiff1d(np.arange(600), [5, 6, 7])
+    np.testing.assert_array_equal(o[fb], plain[fb])
+    np.testing.assert_array_equal(c[fb], 0.0)
+    keep = np.nonzero(~fb)[0]
     X = (raw[keep].astype(np.float64) - mu) / sd
     y, _ = omlp.forward(theta.double().numpy(), X, weights="fp32" if precision == "fp32" else "bf16",
                         act="exact" if precision == "fp32" else "bf16")
     want = y * tsd + tmu
-    np.testing.assert_allclose(c[keep], want, rtol=2e-5, atol=2e-5 * np.abs(want).max())
+    if precision == "fp32":
+        np.testing.assert_allclose(c[keep], want, rtol=2e-5, atol=2e-5 * np.abs(want).max())
+    else:
+        # a float32 h1 and its float64 counterpart can round to neighbouring
+        # bf16 values in a few of the 2.6e6 roundings: rms and a loose maximum
+        assert rms_rel(c[keep], want) <= 2e-5
+        assert np.abs(c[keep] - want).max() <= 1e-3 * np.abs(want).max()   # one flipped bf16 ulp
     np.testing.assert_allclose(o[keep], plain[keep] + c[keep], rtol=1e-6, atol=1e-9)
 
 
