@@ -185,6 +185,41 @@ __device__ __forceinline__ void lattice_position(const TargetRing &t, int q, int
     }
 }
 
+// The same lattice position with the division by 2 q0 done by a
+// multiply-high (set up once per target): m = floor((2^32 - 1) / den) + 1
+// overestimates 1 / den by less than 2^-32, so for num < 2^31 the estimate
+// is the quotient or one more, fixed by the sign of the remainder.
+struct LatticeDiv {
+    uint32_t den, m;
+    float inv;
+};
+
+__device__ __forceinline__ LatticeDiv lattice_div(const TargetRing &t) {
+    LatticeDiv d;
+    d.den = 2u * (uint32_t)t.q0;
+    d.m = (uint32_t)(0xFFFFFFFFull / d.den) + 1u;
+    d.inv = 1.0f / (float)d.den;
+    return d;
+}
+
+__device__ __forceinline__ void lattice_position(const TargetRing &t, const LatticeDiv &d, int q, int &Xi,
+                                                 float &Xf) {
+    if (q == t.q0) {
+        Xi = t.j0;
+        Xf = 0.5f * (float)t.s0;
+        return;
+    }
+    const uint32_t num = (uint32_t)((2 * t.j0 + t.s0) * q);     // < 2^30 for nside <= 8192
+    uint32_t qi = __umulhi(num, d.m);
+    int rem = (int)(num - qi * d.den);
+    if (rem < 0) {
+        qi -= 1u;
+        rem += (int)d.den;
+    }
+    Xi = (int)qi;
+    Xf = (float)rem * d.inv;
+}
+
 __device__ __forceinline__ void window(const RingPair &R, float fr, int &kl, int &kh) {
     if (R.flags & RP_WHOLE) {
         kl = (int)floorf(-0.5f * (float)R.nr - fr) + 1;

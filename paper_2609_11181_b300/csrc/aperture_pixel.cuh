@@ -95,17 +95,18 @@ __device__ __forceinline__ void pixel_pair(const MapArgs &a, const RingPair &R, 
 // the hot loop.
 template <int KIND, int MODE>
 __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
-                                                int64_t pix, const float4 *qtab, float &pe, float &pb, float &pv,
-                                                float &pw, int &nn, int &nm) {
+                                                const LatticeDiv &ld, int64_t pix, const float4 *qtab, float &pe,
+                                                float &pb, float &pv, float &pw, int &nn, int &nm) {
     const int q = R.nr >> 2;
     int Xi;
     float Xf;
-    lattice_position(tr, q, Xi, Xf);
+    lattice_position(tr, ld, q, Xi, Xf);
     const float fr = ((R.flags & RP_SHIFTED) ? 0.5f : 0.0f) - Xf;
     int kl, kh;
     window(R, fr, kl, kh);
-    int kk0 = (Xi + kl) % R.nr;
-    if (kk0 < 0) kk0 += R.nr;
+    // 0 <= Xi < nr and kl > -nr: one correction brings the start into [0, nr)
+    int kk0 = Xi + kl;
+    kk0 += kk0 < 0 ? R.nr : (kk0 >= R.nr ? -R.nr : 0);
     const float u0 = fr * R.dphi;
     int def0 = -1, def1 = -1, ndef = 0;
     float ud0 = 0.f, ud1 = 0.f;
@@ -432,6 +433,7 @@ template <int KIND>
 __device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, const float4 *qtab) {
     const int64_t pix = a.targets[t];
     const TargetRing tr = target_ring(a.N0, pix);
+    const LatticeDiv ld = lattice_div(tr);
     const int64_t row0 = (int64_t)(tr.i0 - 1) * a.kmax;
     const int nent = a.counts[tr.i0 - 1];
     float SE = 0.f, cSE = 0.f, SB = 0.f, cSB = 0.f, SV = 0.f, SW = 0.f, cSW = 0.f;
@@ -441,9 +443,9 @@ __device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, cons
         const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
         float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
         int nn = 0, nm = 0;
-        if (mode == 0) general_segment<KIND, 0>(a, R, tr, pix, qtab, pe, pb, pv, pw, nn, nm);
-        else if (mode == 1) general_segment<KIND, 1>(a, R, tr, pix, qtab, pe, pb, pv, pw, nn, nm);
-        else general_segment<KIND, 2>(a, R, tr, pix, qtab, pe, pb, pv, pw, nn, nm);
+        if (mode == 0) general_segment<KIND, 0>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, nn, nm);
+        else if (mode == 1) general_segment<KIND, 1>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, nn, nm);
+        else general_segment<KIND, 2>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, nn, nm);
         kahan_add(SE, cSE, pe);
         kahan_add(SB, cSB, pb);
         SV += pv;
