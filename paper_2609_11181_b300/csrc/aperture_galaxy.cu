@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
     }
     const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
     const int nent = a.counts[tr0.i0 - 1];
+    const LatticeDiv ld = lattice_div(tr0);
     for (int e = 0; e < nent; ++e) {
         const RingPair Rp = a.table[row0 + e];
         const GalRing R = gal_ring(Rp);
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
         for (int r = 0; r < GT; ++r) {
             TargetRing t = tr0;
             t.j0 = j0[r];
-            lattice_position(t, q, Xi[r], Xf[r]);
+            lattice_position(t, ld, q, Xi[r], Xf[r]);
             if (on[r]) {
                 int kl, kh;
                 window(Rp, R.fr_shift - Xf[r], kl, kh);
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
             nn[r] = 0;
         }
         // pixel range [ulo, uhi] -> at most two runs of ring pixels
-        int lo = ulo % Rp.nr;
-        if (lo < 0) lo += Rp.nr;
+        // ulo lies in (-nr, 2 nr): one correction brings it into [0, nr)
+        const int lo = ulo < 0 ? ulo + Rp.nr : (ulo >= Rp.nr ? ulo - Rp.nr : ulo);
         const int len = uhi - ulo + 1;
         if (R.small) gal_segment<KIND, true>(a, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn);
         else gal_segment<KIND, false>(a, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn);
