@@ -72,6 +72,10 @@ def lib():
         L.orc_finalise.argtypes = [i64, dbl, ip, ip, ip, ip, ip, ip, ip]
         L.orc_bin_catalog.argtypes = [i64, i64, ip, ip, ip, ip, ip,
                                       ip, ip, ip, ip, ip, ip, ip, ip]
+        L.orc_barycentres.argtypes = [i64, ip, ip, ip, ip, ip, ip]
+        L.orc_aperture_points.argtypes = [i64, ip, i64, ip, ip, ip, ip, ip, ip,
+                                          ctypes.c_int, dbl, dbl,
+                                          ip, ip, ip, ip, ip, ip]
         _lib = L
     return _lib
 
@@ -262,6 +266,42 @@ def bin_catalog(nside: int, ra, dec, e1, e2, w) -> dict:
     lib().orc_bin_catalog(nside, n, _p(ra), _p(dec), _p(e1), _p(e2), _p(w),
                           _p(pix), _p(perm), _p(offsets), _p(G1), _p(G2), _p(W), _p(S2), _p(n_p))
     return dict(pix=pix, perm=perm, offsets=offsets, G1=G1, G2=G2, W=W, S2=S2, n=n_p)
+
+
+def barycentres(nside: int, ra, dec, w, binned: dict) -> dict:
+    """Pixels holding galaxies and their w-weighted mean unit vectors (Sect. 3.3),
+    summed in the order of bin_catalog's permutation."""
+    ra, dec, w = (_f64(a).ravel() for a in (ra, dec, w))
+    npix = 12 * nside * nside
+    vec = np.zeros((npix, 3))
+    lib().orc_barycentres(nside, _p(ra), _p(dec), _p(w), _p(_i64(binned["perm"])), _p(_i64(binned["offsets"])),
+                          _p(vec))
+    pix = np.nonzero(binned["n"] > 0)[0]
+    return dict(pix=pix, vec=np.ascontiguousarray(vec[pix]))
+
+
+def aperture_points(centres, vec, G1, G2, W, S2, n_p, kind, theta_ap, xc=0.15):
+    """Sums at unit-vector centres over weighted points (barycentre form, Sect. 3.3)."""
+    c = _f64(centres).reshape(-1, 3)
+    v = _f64(vec).reshape(-1, 3)
+    G1, G2, W, S2 = (_f64(a).ravel() for a in (G1, G2, W, S2))
+    n_p = _i64(n_p).ravel()
+    n0, m = c.shape[0], v.shape[0]
+    SE, SB, SV, SW = (np.empty(n0) for _ in range(4))
+    N = np.empty(n0, dtype=np.int64)
+    K = np.empty(n0, dtype=np.int64)
+    lib().orc_aperture_points(n0, _p(c), m, _p(v), _p(G1), _p(G2), _p(W), _p(S2), _p(n_p), int(kind), float(xc),
+                              float(theta_ap), _p(SE), _p(SB), _p(SV), _p(SW), _p(N), _p(K))
+    return dict(SE=SE, SB=SB, SV=SV, SW=SW, N=N, K=K)
+
+
+def map_barycentre(centres, nside_bin, ra, dec, e1, e2, w, kind, theta_ap, xc=0.15):
+    """The barycentre form of the pixel-based map (Sect. 3.3, sphS_pixB), summed normalisation."""
+    b = bin_catalog(nside_bin, ra, dec, e1, e2, w)
+    bc = barycentres(nside_bin, ra, dec, w, b)
+    p = bc["pix"]
+    return finalise(aperture_points(centres, bc["vec"], b["G1"][p], b["G2"][p], b["W"][p], b["S2"][p], b["n"][p],
+                                    kind, theta_ap, xc), theta_ap)
 
 
 def rms_rel(a, b) -> float:

@@ -328,6 +328,12 @@ static int aperture_term(const orc_cfg *cfg, const double *r0, const double *p,
     double x = ehat[0] * r0[0] + ehat[1] * r0[1] + ehat[2] * r0[2];
     double y = nhat[0] * r0[0] + nhat[1] * r0[1] + nhat[2] * r0[2];
     double den = x * x + y * y;
+    if (den == 0.0) {
+        /* a point within rounding of the centre: no direction, no shear */
+        *c2 = 0.0;
+        *s2 = 0.0;
+        return 1;
+    }
     *c2 = (y * y - x * x) / den;                /* cos 2 psi */
     *s2 = -2.0 * x * y / den;                   /* sin 2 psi */
     return 1;
@@ -341,6 +347,108 @@ static int cmp_dbl_idx(const void *a, const void *b)
     if (x[1] < y[1]) return -1;
     if (x[1] > y[1]) return 1;
     return 0;
+}
+
+/*
+ * Pixel barycentres (Sect. 3.3): for every pixel holding galaxies, the
+ * w-weighted mean of the galaxies' unit vectors, normalised to the sphere
+ * (the paper averages RA and Dec; the mean of unit vectors agrees with that
+ * to second order in the pixel size and has no RA wrap).  The sum runs over
+ * the galaxies in the order of perm (pixel-sorted, input order within a
+ * pixel), one product and one addition at a time.  vec[3 p .. 3 p + 2] is
+ * written for pixels with galaxies; other entries are left as they are.
+ */
+void orc_barycentres(int64_t nside, const double *ra, const double *dec, const double *w,
+                     const int64_t *perm, const int64_t *offsets, double *vec)
+{
+    int64_t npix = 12 * nside * nside;
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t p = 0; p < npix; ++p) {
+        if (offsets[p + 1] == offsets[p]) continue;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int64_t a = offsets[p]; a < offsets[p + 1]; ++a) {
+            int64_t k = perm[a];
+            double r[3];
+            orc_radec2vec(ra[k], dec[k], r);
+            sx = sx + w[k] * r[0];
+            sy = sy + w[k] * r[1];
+            sz = sz + w[k] * r[2];
+        }
+        double nrm = sqrt((sx * sx + sy * sy) + sz * sz);
+        vec[3 * p] = sx / nrm;
+        vec[3 * p + 1] = sy / nrm;
+        vec[3 * p + 2] = sz / nrm;
+    }
+}
+
+/*
+ * Aperture sums over weighted points: the barycentre form of the pixel-based
+ * map (Sect. 3.3, sphS_pixB).  Point k sits at the unit vector v[3k..] and
+ * carries its pixel's sums G1 = sum w e1, G2 = sum w e2, W = sum w,
+ * S2 = sum w^2 |e|^2 and galaxy count np[k].  Membership by the point's
+ * position (s^2 <= T), as for galaxies:
+ *   SE = sum (G1 cos 2psi + G2 sin 2psi) Q,  SB = sum (-G1 sin 2psi + G2 cos 2psi) Q,
+ *   SV = sum S2 Q^2,  SW = sum W,  N = sum np,  K = number of member points.
+ * The local East / North of a point come from its unit vector.
+ */
+void orc_aperture_points(int64_t n0, const double *c, int64_t m, const double *v,
+                         const double *G1, const double *G2, const double *W,
+                         const double *S2, const int64_t *np,
+                         int kind, double xc, double theta_ap,
+                         double *SE, double *SB, double *SV, double *SW,
+                         int64_t *N, int64_t *K)
+{
+    orc_cfg cfg;
+    cfg.kind = kind;
+    cfg.xc = xc;
+    cfg.theta_ap = theta_ap;
+    double sh = sin(0.5 * theta_ap);
+    cfg.T = 4.0 * sh * sh;
+    double *gv = (double *)malloc(sizeof(double) * 9 * (size_t)(m > 0 ? m : 1));
+    double *zi = (double *)malloc(sizeof(double) * 2 * (size_t)(m > 0 ? m : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < m; ++k) {
+        const double *p = v + 3 * k;
+        double *g = gv + 9 * k;
+        double rho = sqrt(p[0] * p[0] + p[1] * p[1]);
+        double ca = rho > 0.0 ? p[0] / rho : 1.0, sa = rho > 0.0 ? p[1] / rho : 0.0;
+        g[0] = p[0]; g[1] = p[1]; g[2] = p[2];
+        g[3] = -sa;        g[4] = ca;         g[5] = 0.0;      /* East  */
+        g[6] = -p[2] * ca; g[7] = -p[2] * sa; g[8] = rho;      /* North */
+    }
+    for (int64_t k = 0; k < m; ++k) {
+        zi[2 * k] = gv[9 * k + 2];
+        zi[2 * k + 1] = (double)k;
+    }
+    qsort(zi, (size_t)m, 2 * sizeof(double), cmp_dbl_idx);
+    double band = sqrt(cfg.T) * (1.0 + 1e-9) + 1e-15;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n0; ++t) {
+        const double *r0 = c + 3 * t;
+        double zlo = r0[2] - band, zhi = r0[2] + band;
+        int64_t lo = 0, hi = m;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (zi[2 * mid] < zlo) lo = mid + 1; else hi = mid;
+        }
+        double se = 0, sb = 0, sv = 0, sw = 0;
+        int64_t cnt = 0, mem = 0;
+        for (int64_t q = lo; q < m && zi[2 * q] <= zhi; ++q) {
+            int64_t k = (int64_t)zi[2 * q + 1];
+            const double *g = gv + 9 * k;
+            double qv, c2, s2;
+            if (!aperture_term(&cfg, r0, g, g + 3, g + 6, &qv, &c2, &s2)) continue;
+            se += (G1[k] * c2 + G2[k] * s2) * qv;
+            sb += (-G1[k] * s2 + G2[k] * c2) * qv;
+            sv += S2[k] * qv * qv;
+            sw += W[k];
+            cnt += np[k];
+            mem += 1;
+        }
+        SE[t] = se; SB[t] = sb; SV[t] = sv; SW[t] = sw; N[t] = cnt; K[t] = mem;
+    }
+    free(gv);
+    free(zi);
 }
 
 /*

@@ -301,3 +301,89 @@ def test_own_pixel_carries_no_shear(kind):
         assert r["SW"][0] == 5.0 and r["N"][0] == 5
         q0 = oracle.filter_q(kind, 0.0)[0] / (20 * ARCMIN) ** 2
         assert r["SV"][0] == pytest.approx(q0 * q0 * 0.7, rel=1e-12, abs=1e-300)
+
+
+# --------------------------------------------------------------------------
+# barycentre form of the pixel-based map (Sect. 3.3)
+# --------------------------------------------------------------------------
+def _spread_catalog(seed, nside, ra0, dec0, rad_deg, per_pixel_max_one=True, n=3000):
+    """Galaxies at most one per pixel (drawn pixel by pixel inside a cap)."""
+    rng = np.random.default_rng(seed)
+    v = oracle.pix2vec(nside, np.arange(12 * nside * nside))
+    c = oracle.radec2vec([ra0], [dec0])[0]
+    pix = np.nonzero(v @ c >= np.cos(np.radians(rad_deg)))[0]
+    pick = rng.choice(pix, size=min(n, pix.size), replace=False)
+    # a point near each picked centre, well inside its pixel
+    pv = v[pick] + rng.normal(0, 0.05 * np.sqrt(4 * np.pi / (12 * nside * nside)), (pick.size, 3))
+    pv /= np.linalg.norm(pv, axis=1)[:, None]
+    ra = np.degrees(np.arctan2(pv[:, 1], pv[:, 0])) % 360.0
+    dec = np.degrees(np.arcsin(np.clip(pv[:, 2], -1, 1)))
+    keep = oracle.ang2pix(nside, ra, dec) == pick
+    ra, dec = ra[keep], dec[keep]
+    e1 = rng.normal(0, 0.26, ra.size)
+    e2 = rng.normal(0, 0.26, ra.size)
+    w = rng.uniform(0.5, 1.5, ra.size)
+    return ra, dec, e1, e2, w
+
+
+def test_barycentre_map_equals_brute_force_with_one_galaxy_per_pixel():
+    nside = 256
+    ra, dec, e1, e2, w = _spread_catalog(11, nside, 30.0, 20.0, 3.0)
+    assert np.bincount(oracle.ang2pix(nside, ra, dec)).max() == 1
+    tg = oracle.pix2vec(64, np.arange(12 * 64 * 64))
+    c = oracle.radec2vec([30.0], [20.0])[0]
+    tg = tg[tg @ c >= np.cos(np.radians(1.5))]
+    th = 40.0 * ARCMIN
+    bf = oracle.map_galaxies(tg, ra, dec, e1, e2, w, 2, th)
+    pb = oracle.map_barycentre(tg, nside, ra, dec, e1, e2, w, 2, th)
+    np.testing.assert_array_equal(pb["N"], bf["N"])
+    np.testing.assert_array_equal(pb["K"], bf["N"])
+    for k in ("ME", "MB", "VAR", "SW"):
+        np.testing.assert_allclose(pb[k], bf[k], rtol=1e-10, atol=1e-14)
+
+
+def test_barycentre_map_equals_pixel_map_when_galaxies_sit_at_centres():
+    nside = 128
+    rng = np.random.default_rng(12)
+    v = oracle.pix2vec(nside, np.arange(12 * nside * nside))
+    c = oracle.radec2vec([200.0], [-40.0])[0]
+    pix = np.nonzero(v @ c >= np.cos(np.radians(6.0)))[0]
+    pick = rng.choice(pix, size=4000)                       # repeats: several galaxies per pixel
+    pv = v[pick]
+    ra = np.degrees(np.arctan2(pv[:, 1], pv[:, 0])) % 360.0
+    dec = np.degrees(np.arcsin(pv[:, 2]))
+    e1, e2 = rng.normal(0, 0.26, pick.size), rng.normal(0, 0.26, pick.size)
+    w = rng.uniform(0.5, 1.5, pick.size)
+    # targets on the coarser grid: their centres are never bin-pixel centres
+    t64 = oracle.pix2vec(64, np.arange(12 * 64 * 64))
+    tg = t64[t64 @ c >= np.cos(np.radians(5.0))]
+    th = 50.0 * ARCMIN
+    b = oracle.bin_catalog(nside, ra, dec, e1, e2, w)
+    bc = oracle.barycentres(nside, ra, dec, w, b)
+    # the barycentre of points at a pixel's centre is that centre
+    np.testing.assert_allclose(bc["vec"], v[bc["pix"]], rtol=0, atol=1e-14)
+    px = oracle.map_pixels(tg, nside, b["G1"], b["G2"], b["W"], b["S2"], b["n"], 2, th)
+    pb = oracle.map_barycentre(tg, nside, ra, dec, e1, e2, w, 2, th)
+    np.testing.assert_array_equal(pb["N"], px["N"])
+    for k in ("ME", "MB", "VAR", "SW"):
+        np.testing.assert_allclose(pb[k], px[k], rtol=1e-9, atol=1e-12)
+
+
+def test_barycentre_is_the_weighted_mean_direction():
+    # two galaxies in one pixel: the barycentre lies on the great-circle arc
+    # between them, dividing it in the ratio of the weights (tan relation)
+    nside = 4
+    p0 = 100
+    r = oracle.pix2vec(nside, [p0])[0]
+    east = np.array([-r[1], r[0], 0.0]) / np.hypot(r[0], r[1])
+    pa = r + 0.02 * east
+    pb_ = r - 0.02 * east
+    pts = np.stack([pa, pb_]) / np.linalg.norm(np.stack([pa, pb_]), axis=1)[:, None]
+    ra = np.degrees(np.arctan2(pts[:, 1], pts[:, 0])) % 360.0
+    dec = np.degrees(np.arcsin(pts[:, 2]))
+    assert (oracle.ang2pix(nside, ra, dec) == p0).all()
+    w = np.array([3.0, 1.0])
+    b = oracle.bin_catalog(nside, ra, dec, np.zeros(2), np.zeros(2), w)
+    bc = oracle.barycentres(nside, ra, dec, w, b)
+    want = (3.0 * pts[0] + pts[1]) / np.linalg.norm(3.0 * pts[0] + pts[1])
+    np.testing.assert_allclose(bc["vec"][0], want, rtol=0, atol=1e-12)
