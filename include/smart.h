@@ -161,6 +161,19 @@ smart_status smart_map_bruteforce(smart_ctx *ctx, const smart_maps *out);
  */
 smart_status smart_map_pixel(smart_ctx *ctx, const smart_maps *out);
 
+/*
+ * Pixel-based map with each bin pixel placed at its galaxies' barycentre
+ * (Sect. 3.3, sphS_pixB).  Needs smart_bin_galaxies.  Every bin pixel that
+ * holds galaxies becomes one point at the w-weighted mean of its galaxies'
+ * unit vectors (float64, normalised) carrying the pixel's sums G1, G2, W,
+ * S2; points are members when their barycentre lies within theta_ap of the
+ * target (float64 decision near the edge, as for galaxies), and the sums are
+ * normalised like the other maps.  out->count = galaxies in member pixels,
+ * out->members = member pixels.  The records are built once per catalogue.
+ */
+smart_status smart_map_barycentre(smart_ctx *ctx, const smart_maps *out);
+
+
 /* ---- batched pixel-based maps ----------------------------------------- */
 
 typedef struct smart_batch smart_batch;
@@ -245,7 +258,9 @@ typedef enum {
     SMART_KT_BIN_SORT = 6,         /* smart_bin_galaxies: every radix pass */
     SMART_KT_BIN_RECORDS = 7,      /* smart_bin_galaxies: permuted galaxy records */
     SMART_KT_BIN_PIXEL_SUMS = 8,   /* smart_bin_galaxies: per-pixel sums */
-    SMART_KT_COUNT = 9
+    SMART_KT_BARY_BUILD = 9,       /* smart_map_barycentre: barycentre records (once per catalogue) */
+    SMART_KT_BARY_MAP = 10,        /* smart_map_barycentre: main kernel */
+    SMART_KT_COUNT = 11
 } smart_kernel_id;
 
 /*

@@ -167,6 +167,12 @@ class Context:
         self._check(self._lib.smart_map_pixel(self._h, ctypes.byref(m)), "smart_map_pixel")
         return out
 
+    def map_barycentre(self, out: dict | None = None) -> dict:
+        """Pixel-based map with the bin pixels at their galaxies' barycentres (needs bin_galaxies)."""
+        out, m = self._out(out)
+        self._check(self._lib.smart_map_barycentre(self._h, ctypes.byref(m)), "smart_map_barycentre")
+        return out
+
     def map_bruteforce(self, out: dict | None = None) -> dict:
         out, m = self._out(out)
         self._check(self._lib.smart_map_bruteforce(self._h, ctypes.byref(m)), "smart_map_bruteforce")

@@ -112,6 +112,15 @@ __device__ __forceinline__ int warp_sum_i(int v) {
     return v;
 }
 
+// Extra inputs of the barycentre form (Sect. 3.3): the records are bin
+// pixels placed at their barycentres; cnt = galaxies of each record's pixel,
+// vec = the float64 barycentre (3 per record), raw_m = member records per target.
+struct BaryArgs {
+    const int32_t *cnt;
+    const double *vec;
+    int32_t *raw_m;
+};
+
 // A pair inside the float32 guard band, set aside for the float64 decision.
 struct BandPair {
     int64_t target;     // index into the target list
@@ -124,11 +133,11 @@ struct BandPair {
 // target.  The per-target body has no branch on membership (non-members add
 // zeros), so the GT independent chains can interleave; guard-band pairs take
 // a rare branch to the float64 list.
-template <int KIND, bool SMALL>
-__device__ __forceinline__ void gal_segment(const MapArgs &a, const RingPair &Rp, const GalRing &R, int e, int lane,
-                                            int64_t tb, const bool (&on)[GT], const int (&Xi)[GT],
+template <int KIND, bool SMALL, bool BARY>
+__device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba, const RingPair &Rp, const GalRing &R,
+                                            int e, int lane, int64_t tb, const bool (&on)[GT], const int (&Xi)[GT],
                                             const float (&Xf)[GT], int lo, int len, float (&pe)[GT], float (&pb)[GT],
-                                            float (&pv)[GT], float (&pw)[GT], int (&nn)[GT]) {
+                                            float (&pv)[GT], float (&pw)[GT], int (&nn)[GT], int (&nm)[GT]) {
     const int n1 = min(len, Rp.nr - lo);
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
@@ -142,6 +151,7 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const RingPair &Rp
             const float4 geo = __ldg(a.geo + g);
             const float4 sh = __ldg(a.shear + g);
             const int kg = (int)__ldg(a.keys + g) - R.start;
+            const int cnt = BARY ? __ldg(ba.cnt + g) : 1;
             float A, B, C, D, frg;
             gal_setup(R, geo, A, B, C, D, frg);
 #pragma unroll
@@ -174,14 +184,15 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const RingPair &Rp
                 pb[r] = fmaf(w, fmaf(sh.y, cc, -sh.x * ss), pb[r]);
                 pv[r] = fmaf(in ? Q * Q : 0.f, sh.w, pv[r]);
                 pw[r] += in ? sh.z : 0.f;
-                nn[r] += in ? 1 : 0;
+                nn[r] += in ? cnt : 0;
+                if (BARY) nm[r] += in ? 1 : 0;
             }
         }
     }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
+template <int KIND, bool BARY>
+__global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a, const BaryArgs ba) {
     const int lane = threadIdx.x & 31;
     const int64_t tile = (int64_t)blockIdx.x * GW + (threadIdx.x >> 5);
     if (tile >= a.n_tiles) return;
@@ -197,11 +208,11 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
         j0[r] = on[r] ? (int)(a.targets[tb + r] - ring_start0) : tr0.j0;
     }
     float SE[GT], cSE[GT], SB[GT], cSB[GT], SV[GT], SW[GT], cSW[GT];
-    int NN[GT];
+    int NN[GT], NM[GT];
 #pragma unroll
     for (int r = 0; r < GT; ++r) {
         SE[r] = cSE[r] = SB[r] = cSB[r] = SV[r] = SW[r] = cSW[r] = 0.f;
-        NN[r] = 0;
+        NN[r] = NM[r] = 0;
     }
     const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
     const int nent = a.counts[tr0.i0 - 1];
@@ -231,18 +242,18 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
             uhi = Rp.nr - 1;
         }
         float pe[GT], pb[GT], pv[GT], pw[GT];
-        int nn[GT];
+        int nn[GT], nm[GT];
 #pragma unroll
         for (int r = 0; r < GT; ++r) {
             pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
-            nn[r] = 0;
+            nn[r] = nm[r] = 0;
         }
         // pixel range [ulo, uhi] -> at most two runs of ring pixels
         // ulo lies in (-nr, 2 nr): one correction brings it into [0, nr)
         const int lo = ulo < 0 ? ulo + Rp.nr : (ulo >= Rp.nr ? ulo - Rp.nr : ulo);
         const int len = uhi - ulo + 1;
-        if (R.small) gal_segment<KIND, true>(a, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn);
-        else gal_segment<KIND, false>(a, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn);
+        if (R.small) gal_segment<KIND, true, BARY>(a, ba, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn, nm);
+        else gal_segment<KIND, false, BARY>(a, ba, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn, nm);
 #pragma unroll
         for (int r = 0; r < GT; ++r) {
             kahan_add(SE[r], cSE[r], pe[r]);
@@ -250,6 +261,7 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
             SV[r] += pv[r];
             kahan_add(SW[r], cSW[r], pw[r]);
             NN[r] += nn[r];
+            NM[r] += nm[r];
         }
     }
     // warp reduction of the per-lane sums (compensation folded in first);
@@ -261,6 +273,7 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
         const float sv = warp_sum(SV[r]);
         const float sw = warp_sum(SW[r] - cSW[r]);
         const int n = warp_sum_i(NN[r]);
+        const int m = BARY ? warp_sum_i(NM[r]) : 0;
         if (lane == r && on[r]) {
             double *raw = a.raw + 4 * (tb + r);
             raw[0] = se;
@@ -268,14 +281,15 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a) {
             raw[2] = sv;
             raw[3] = sw;
             a.raw_n[tb + r] = n;
+            if (BARY) ba.raw_m[tb + r] = m;
         }
     }
 }
 
 // the guard-band pairs: float64 decision, then the float32 contribution is
 // added to the target's raw sums
-template <int KIND>
-__global__ void k_galaxy_band(const MapArgs a) {
+template <int KIND, bool BARY>
+__global__ void k_galaxy_band(const MapArgs a, const BaryArgs ba) {
     const unsigned long long nall = *a.band_count;
     if (nall > (unsigned long long)a.band_cap && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, SMART_STATUS_BAND_OVERFLOW);
     const unsigned long long nb = min(nall, (unsigned long long)a.band_cap);
@@ -283,10 +297,16 @@ __global__ void k_galaxy_band(const MapArgs a) {
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const BandPair bp = reinterpret_cast<const BandPair *>(a.band)[i];
         const int64_t pix = a.targets[bp.target];
-        const double2 rd = a.radec[bp.galaxy];
         double x0, y0, z0, x1, y1, z1;
         pix2vec64(a.N0, pix, x0, y0, z0);
-        radec2vec64(rd.x, rd.y, x1, y1, z1);
+        if (BARY) {
+            x1 = ba.vec[3 * (int64_t)bp.galaxy];
+            y1 = ba.vec[3 * (int64_t)bp.galaxy + 1];
+            z1 = ba.vec[3 * (int64_t)bp.galaxy + 2];
+        } else {
+            const double2 rd = a.radec[bp.galaxy];
+            radec2vec64(rd.x, rd.y, x1, y1, z1);
+        }
         atomicAdd(a.fp64_count, 1ull);
         if (!member64(x0, y0, z0, x1, y1, z1, a.T)) continue;
         const TargetRing tr = target_ring(a.N0, pix);
@@ -307,12 +327,13 @@ __global__ void k_galaxy_band(const MapArgs a) {
         atomicAdd(raw + 1, (double)pb);
         atomicAdd(raw + 2, (double)pv);
         atomicAdd(raw + 3, (double)pw);
-        atomicAdd(a.raw_n + bp.target, 1);
+        atomicAdd(a.raw_n + bp.target, BARY ? ba.cnt[bp.galaxy] : 1);
+        if (BARY) atomicAdd(ba.raw_m + bp.target, 1);
     }
 }
 
 // summed normalisation (Sect. 2.4) from the float64 raw sums
-__global__ void k_galaxy_finalise(const MapArgs a) {
+__global__ void k_galaxy_finalise(const MapArgs a, const int32_t *__restrict__ raw_m) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.n; t += (int64_t)gridDim.x * blockDim.x) {
         const double *raw = a.raw + 4 * t;
         const int n = a.raw_n[t];
@@ -329,7 +350,7 @@ __global__ void k_galaxy_finalise(const MapArgs a) {
         if (a.map_b) a.map_b[t] = mb;
         if (a.var) a.var[t] = vv;
         if (a.count) a.count[t] = n;
-        if (a.members) a.members[t] = n;
+        if (a.members) a.members[t] = raw_m ? raw_m[t] : n;
     }
 }
 
@@ -337,13 +358,154 @@ __global__ void k_galaxy_finalise(const MapArgs a) {
 
 using namespace smart;
 
-extern "C" smart_status smart_map_bruteforce(smart_ctx *c, const smart_maps *out) {
-    if (!c) return SMART_E_ARG;
-    if (!c->have_catalog) return fail(c, SMART_E_STATE, "smart_map_bruteforce: no catalogue (smart_bin_galaxies first)");
+// ------------------------------------------------------------------------
+// barycentre records (Sect. 3.3), built once per catalogue: record r of bin
+// pixel p (r = prefix of the non-empty pixels) holds the float64 unit vector
+// of the w-weighted mean of the pixel's galaxies (products w r, then a sum
+// in catalogue order one addition at a time, then normalised), its float32
+// offsets from the pixel centre in the galaxy-record layout, the pixel sums
+// and the galaxy count.
+// ------------------------------------------------------------------------
+__global__ void k_bary_flags(const int32_t *__restrict__ np, int64_t npix, int32_t *__restrict__ flag) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
+        flag[p] = np[p] > 0 ? 1 : 0;
+}
+
+// per pixel with galaxies: its record index, key, count and sums
+__global__ void k_bary_keys(int64_t npix, const int32_t *__restrict__ boff, const float4 *__restrict__ px,
+                            const int32_t *__restrict__ np, float4 *__restrict__ sh, uint32_t *__restrict__ keys,
+                            int32_t *__restrict__ cnt) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        if (np[p] == 0) continue;
+        const int32_t r = boff[p];
+        const float4 q = px[p];                        // (G1, G2, S2, W)
+        sh[r] = make_float4(q.x, q.y, q.w, q.z);       // record layout (w e1, w e2, w, w^2 |e|^2)
+        keys[r] = (uint32_t)p;
+        cnt[r] = np[p];
+    }
+}
+
+// one warp per record: the lanes turn 32 galaxies at a time into w r
+// (float64), lane 0 adds them in catalogue order, normalises and writes the
+// unit vector and the float32 offsets from the pixel centre
+__global__ void k_bary_vec(int64_t N, int64_t nrec, const uint32_t *__restrict__ keys,
+                           const int32_t *__restrict__ off, const double2 *__restrict__ radec,
+                           const float4 *__restrict__ rec_sh, const double *__restrict__ lat_deg,
+                           float4 *__restrict__ geo, double *__restrict__ vec) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < nrec; r += warps) {
+        const int64_t p = keys[r];
+        const int32_t a = off[p], b = off[p + 1];
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int32_t k0 = a; k0 < b; k0 += 32) {
+            double x = 0.0, y = 0.0, z = 0.0;
+            const int32_t k = k0 + lane;
+            if (k < b) {
+                const double2 rd = radec[k];
+                radec2vec64(rd.x, rd.y, x, y, z);
+                const double w = (double)rec_sh[k].z;
+                x = __dmul_rn(w, x);
+                y = __dmul_rn(w, y);
+                z = __dmul_rn(w, z);
+            }
+            const int m = min(32, b - k0);
+            for (int j = 0; j < m; ++j) {          // catalogue order, one addition at a time
+                const double xj = __shfl_sync(0xffffffffu, x, j);
+                const double yj = __shfl_sync(0xffffffffu, y, j);
+                const double zj = __shfl_sync(0xffffffffu, z, j);
+                sx = __dadd_rn(sx, xj);
+                sy = __dadd_rn(sy, yj);
+                sz = __dadd_rn(sz, zj);
+            }
+        }
+        if (lane != 0) continue;
+        const double nrm = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz)));
+        const double vx = __ddiv_rn(sx, nrm), vy = __ddiv_rn(sy, nrm), vz = __ddiv_rn(sz, nrm);
+        vec[3 * r] = vx;
+        vec[3 * r + 1] = vy;
+        vec[3 * r + 2] = vz;
+        const double rho = sqrt(vx * vx + vy * vy);
+        const double dec = atan2(vz, rho) * (180.0 / SMART_PI);
+        const double ra = atan2(vy, vx) * (180.0 / SMART_PI);
+        const RingPix rp = pix_to_ring(N, p);
+        const double cphi = 90.0 * ring_phi_quarter(N, rp.ring, rp.j);
+        double da = fmod(ra - cphi, 360.0);
+        if (da > 180.0) da -= 360.0;
+        if (da <= -180.0) da += 360.0;
+        const RingGeom rg = ring_geom(N, rp.ring);
+        geo[r] = make_float4((float)((dec - lat_deg[rp.ring]) * (SMART_PI / 180.0)), (float)(da * (double)rg.nr / 360.0),
+                             (float)vz, (float)rho);
+    }
+}
+
+static smart_status build_barycentres(smart_ctx *c) {
+    const int64_t N = c->nside_bin;
+    const int64_t npix = npix_of(N);
+    cudaStream_t s = c->stream;
+    smart_status st = ensure_alloc(c, (void **)&c->bary_off, c->cap_bary_off, npix + 1, sizeof(int32_t), "barycentre offsets");
+    if (st != SMART_OK) return st;
+    // the non-empty flags go to the count-prefix buffer, which a map binned
+    // from the catalogue does not use (its prefix is the catalogue offsets)
+    st = ensure_alloc(c, (void **)&c->np_prefix, c->cap_np_prefix, npix + 1, sizeof(int32_t), "count prefix");
+    if (st != SMART_OK) return st;
+    const unsigned g = (unsigned)std::min<int64_t>((npix + 255) / 256, (int64_t)c->num_sms * 32);
+    {
+        KernelTimer timer(c, SMART_KT_BARY_BUILD);
+        k_bary_flags<<<g, 256, 0, s>>>(c->own_np, npix, c->np_prefix);
+        if ((st = check_cuda(c, cudaGetLastError(), "k_bary_flags")) != SMART_OK) return st;
+        if ((st = exclusive_scan_i32(c, c->np_prefix, c->bary_off, npix, npix + 1)) != SMART_OK) return st;
+    }
+    int32_t nb = 0;
+    if ((st = check_cuda(c, cudaMemcpyAsync(&nb, c->bary_off + npix, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                         "barycentre count")) != SMART_OK)
+        return st;
+    if ((st = check_cuda(c, cudaStreamSynchronize(s), "barycentre count")) != SMART_OK) return st;
+    const int64_t need = std::max<int64_t>(nb, 1);
+    if (need > c->cap_bary) {
+        void *bufs[] = {c->bary_geo, c->bary_sh, c->bary_keys, c->bary_cnt, c->bary_vec};
+        for (void *b : bufs)
+            if (b) cudaFree(b);
+        c->bary_geo = c->bary_sh = nullptr;
+        c->bary_keys = nullptr;
+        c->bary_cnt = nullptr;
+        c->bary_vec = nullptr;
+        c->cap_bary = 0;
+        if (cudaMalloc(&c->bary_geo, need * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&c->bary_sh, need * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc(&c->bary_keys, need * sizeof(uint32_t)) != cudaSuccess ||
+            cudaMalloc(&c->bary_cnt, need * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&c->bary_vec, 3 * need * sizeof(double)) != cudaSuccess)
+            return fail(c, SMART_E_NOMEM, "cudaMalloc(barycentre records) failed");
+        c->cap_bary = need;
+    }
+    c->n_bary = nb;
+    if (nb > 0) {
+        KernelTimer timer(c, SMART_KT_BARY_BUILD);
+        k_bary_keys<<<g, 256, 0, s>>>(npix, c->bary_off, c->own_px, c->own_np, c->bary_sh, c->bary_keys, c->bary_cnt);
+        const unsigned gv = (unsigned)std::min<int64_t>((nb + 7) / 8, (int64_t)c->num_sms * 64);
+        k_bary_vec<<<gv, 256, 0, s>>>(N, nb, c->bary_keys, c->offsets, c->rec_radec, c->rec_shear, c->ring_lat,
+                                      c->bary_geo, c->bary_vec);
+    }
+    if ((st = check_cuda(c, cudaGetLastError(), "barycentre records")) != SMART_OK) return st;
+    c->bary_version = c->catalog_version;
+    return SMART_OK;
+}
+
+// brute force over galaxy records, or over barycentre records
+static smart_status map_records(smart_ctx *c, const smart_maps *out, bool bary) {
+    if (!c->have_catalog)
+        return fail(c, SMART_E_STATE, bary ? "smart_map_barycentre: no catalogue (smart_bin_galaxies first)"
+                                           : "smart_map_bruteforce: no catalogue (smart_bin_galaxies first)");
     MapArgs a{};
     smart_status st = common_args(c, out, a);
     if (st != SMART_OK) return st;
+    if (bary && c->bary_version != c->catalog_version) {
+        st = build_barycentres(c);
+        if (st != SMART_OK) return st;
+    }
     if (!c->rp_gal) {
+        // galaxies and barycentres lie within one bin-pixel radius of their pixel centre
         const double th = c->theta_ap + max_pixrad(c->nside_bin) * 1.01 + 1e-9;
         st = build_ring_pairs(c, th, &c->rp_gal, &c->rp_gal_cnt, &c->kmax_gal);
         if (st != SMART_OK) return st;
@@ -359,14 +521,22 @@ extern "C" smart_status smart_map_bruteforce(smart_ctx *c, const smart_maps *out
     const int64_t band_cap = std::max<int64_t>(1 << 20, 16 * n);
     st = ensure_alloc(c, (void **)&c->band, c->cap_band, band_cap, sizeof(BandPair), "guard-band list");
     if (st != SMART_OK) return st;
+    BaryArgs ba{};
+    if (bary) {
+        st = ensure_alloc(c, (void **)&c->raw_m, c->cap_raw_m, n + 1, sizeof(int32_t), "member records");
+        if (st != SMART_OK) return st;
+        ba.cnt = c->bary_cnt;
+        ba.vec = c->bary_vec;
+        ba.raw_m = c->raw_m;
+    }
     a.table = c->rp_gal;
     a.counts = c->rp_gal_cnt;
     a.kmax = c->kmax_gal;
-    a.offsets = c->offsets;
-    a.geo = c->rec_geo;
-    a.shear = c->rec_shear;
-    a.radec = c->rec_radec;
-    a.keys = c->keys;
+    a.offsets = bary ? c->bary_off : c->offsets;
+    a.geo = bary ? c->bary_geo : c->rec_geo;
+    a.shear = bary ? c->bary_sh : c->rec_shear;
+    a.radec = bary ? nullptr : c->rec_radec;
+    a.keys = bary ? c->bary_keys : c->keys;
     a.tiles = c->gal_tiles;
     a.n_tiles = c->n_gal_tiles;
     a.raw = c->raw;
@@ -378,20 +548,41 @@ extern "C" smart_status smart_map_bruteforce(smart_ctx *c, const smart_maps *out
     cudaMemsetAsync(c->d_band_count, 0, sizeof(unsigned long long), c->stream);
     if (n == 0) return SMART_OK;
     const unsigned blocks = (unsigned)((a.n_tiles + GW - 1) / GW);
-    {
+    const bool poly = c->filter_kind == SMART_FILTER_POLY;
+    if (bary) {
+        KernelTimer timer(c, SMART_KT_BARY_MAP);
+        if (poly) k_map_galaxy<SMART_FILTER_POLY, true><<<blocks, 32 * GW, 0, c->stream>>>(a, ba);
+        else k_map_galaxy<SMART_FILTER_SCHIRMER, true><<<blocks, 32 * GW, 0, c->stream>>>(a, ba);
+    } else {
         KernelTimer timer(c, SMART_KT_GALAXY);
-        if (c->filter_kind == SMART_FILTER_POLY) k_map_galaxy<SMART_FILTER_POLY><<<blocks, 32 * GW, 0, c->stream>>>(a);
-        else k_map_galaxy<SMART_FILTER_SCHIRMER><<<blocks, 32 * GW, 0, c->stream>>>(a);
+        if (poly) k_map_galaxy<SMART_FILTER_POLY, false><<<blocks, 32 * GW, 0, c->stream>>>(a, ba);
+        else k_map_galaxy<SMART_FILTER_SCHIRMER, false><<<blocks, 32 * GW, 0, c->stream>>>(a, ba);
     }
     {
         KernelTimer timer(c, SMART_KT_GALAXY_BAND);
-        if (c->filter_kind == SMART_FILTER_POLY) k_galaxy_band<SMART_FILTER_POLY><<<(unsigned)c->num_sms, 256, 0, c->stream>>>(a);
-        else k_galaxy_band<SMART_FILTER_SCHIRMER><<<(unsigned)c->num_sms, 256, 0, c->stream>>>(a);
+        const unsigned gb = (unsigned)c->num_sms;
+        if (bary) {
+            if (poly) k_galaxy_band<SMART_FILTER_POLY, true><<<gb, 256, 0, c->stream>>>(a, ba);
+            else k_galaxy_band<SMART_FILTER_SCHIRMER, true><<<gb, 256, 0, c->stream>>>(a, ba);
+        } else {
+            if (poly) k_galaxy_band<SMART_FILTER_POLY, false><<<gb, 256, 0, c->stream>>>(a, ba);
+            else k_galaxy_band<SMART_FILTER_SCHIRMER, false><<<gb, 256, 0, c->stream>>>(a, ba);
+        }
     }
     const unsigned fb = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 16);
     {
         KernelTimer timer(c, SMART_KT_GALAXY_FINALISE);
-        k_galaxy_finalise<<<fb, 256, 0, c->stream>>>(a);
+        k_galaxy_finalise<<<fb, 256, 0, c->stream>>>(a, bary ? c->raw_m : nullptr);
     }
-    return check_cuda(c, cudaGetLastError(), "brute-force launches");
+    return check_cuda(c, cudaGetLastError(), bary ? "barycentre launches" : "brute-force launches");
+}
+
+extern "C" smart_status smart_map_bruteforce(smart_ctx *c, const smart_maps *out) {
+    if (!c) return SMART_E_ARG;
+    return map_records(c, out, false);
+}
+
+extern "C" smart_status smart_map_barycentre(smart_ctx *c, const smart_maps *out) {
+    if (!c) return SMART_E_ARG;
+    return map_records(c, out, true);
 }

@@ -393,6 +393,7 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     c->binned_from_catalog = true;
     c->have_catalog = true;
     c->n_gal = n;
+    c->catalog_version += 1;
     int inv = 0;
     cudaMemcpyAsync(&inv, c->d_invalid, sizeof(int), cudaMemcpyDeviceToHost, s);
     if ((st = check_cuda(c, cudaStreamSynchronize(s), "smart_bin_galaxies")) != SMART_OK) return st;

@@ -351,6 +351,19 @@ struct smart_ctx {
     int *d_status = nullptr;                         // device status word
     int num_sms = 148;
 
+    // barycentre form of the pixel map (Sect. 3.3): one record per bin pixel
+    // holding galaxies, in the layout of the galaxy records
+    int64_t catalog_version = 0, bary_version = -1;
+    int32_t *bary_off = nullptr;                     // npix + 1: record of each pixel (prefix of n_p > 0)
+    int64_t cap_bary_off = 0;
+    float4 *bary_geo = nullptr, *bary_sh = nullptr;
+    uint32_t *bary_keys = nullptr;
+    int32_t *bary_cnt = nullptr;                     // galaxies of the record's pixel
+    double *bary_vec = nullptr;                      // float64 unit vector, 3 per record
+    int64_t n_bary = 0, cap_bary = 0;
+    int32_t *raw_m = nullptr;                        // member records per target
+    int64_t cap_raw_m = 0;
+
     // diagnostics
     unsigned long long *d_fp64_count = nullptr;
     bool timing = false;                             // record events around each kernel launch
