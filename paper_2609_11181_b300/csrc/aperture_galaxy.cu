@@ -385,41 +385,35 @@ __global__ void k_bary_keys(int64_t npix, const int32_t *__restrict__ boff, cons
     }
 }
 
-// one warp per record: the lanes turn 32 galaxies at a time into w r
-// (float64), lane 0 adds them in catalogue order, normalises and writes the
-// unit vector and the float32 offsets from the pixel centre
+// w r of every galaxy (float64, one thread per galaxy)
+__global__ void k_bary_wr(int64_t n, const double2 *__restrict__ radec, const float4 *__restrict__ rec_sh,
+                          double *__restrict__ wr) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double2 rd = radec[k];
+        double x, y, z;
+        radec2vec64(rd.x, rd.y, x, y, z);
+        const double w = (double)rec_sh[k].z;
+        wr[3 * k] = __dmul_rn(w, x);
+        wr[3 * k + 1] = __dmul_rn(w, y);
+        wr[3 * k + 2] = __dmul_rn(w, z);
+    }
+}
+
+// one thread per record: the pixel's w r added in catalogue order (one
+// addition at a time), normalised; the unit vector and the float32 offsets
+// from the pixel centre are written
 __global__ void k_bary_vec(int64_t N, int64_t nrec, const uint32_t *__restrict__ keys,
-                           const int32_t *__restrict__ off, const double2 *__restrict__ radec,
-                           const float4 *__restrict__ rec_sh, const double *__restrict__ lat_deg,
-                           float4 *__restrict__ geo, double *__restrict__ vec) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < nrec; r += warps) {
+                           const int32_t *__restrict__ off, const double *__restrict__ wr,
+                           const double *__restrict__ lat_deg, float4 *__restrict__ geo, double *__restrict__ vec) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrec; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = keys[r];
         const int32_t a = off[p], b = off[p + 1];
         double sx = 0.0, sy = 0.0, sz = 0.0;
-        for (int32_t k0 = a; k0 < b; k0 += 32) {
-            double x = 0.0, y = 0.0, z = 0.0;
-            const int32_t k = k0 + lane;
-            if (k < b) {
-                const double2 rd = radec[k];
-                radec2vec64(rd.x, rd.y, x, y, z);
-                const double w = (double)rec_sh[k].z;
-                x = __dmul_rn(w, x);
-                y = __dmul_rn(w, y);
-                z = __dmul_rn(w, z);
-            }
-            const int m = min(32, b - k0);
-            for (int j = 0; j < m; ++j) {          // catalogue order, one addition at a time
-                const double xj = __shfl_sync(0xffffffffu, x, j);
-                const double yj = __shfl_sync(0xffffffffu, y, j);
-                const double zj = __shfl_sync(0xffffffffu, z, j);
-                sx = __dadd_rn(sx, xj);
-                sy = __dadd_rn(sy, yj);
-                sz = __dadd_rn(sz, zj);
-            }
+        for (int32_t k = a; k < b; ++k) {
+            sx = __dadd_rn(sx, wr[3 * (int64_t)k]);
+            sy = __dadd_rn(sy, wr[3 * (int64_t)k + 1]);
+            sz = __dadd_rn(sz, wr[3 * (int64_t)k + 2]);
         }
-        if (lane != 0) continue;
         const double nrm = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz)));
         const double vx = __ddiv_rn(sx, nrm), vy = __ddiv_rn(sy, nrm), vz = __ddiv_rn(sz, nrm);
         vec[3 * r] = vx;
@@ -481,11 +475,16 @@ static smart_status build_barycentres(smart_ctx *c) {
     }
     c->n_bary = nb;
     if (nb > 0) {
+        // w r of every galaxy: float64 scratch of 24 bytes per galaxy
+        st = ensure_alloc(c, (void **)&c->bary_wr, c->cap_bary_wr, 3 * c->n_gal, sizeof(double), "barycentre scratch");
+        if (st != SMART_OK) return st;
         KernelTimer timer(c, SMART_KT_BARY_BUILD);
         k_bary_keys<<<g, 256, 0, s>>>(npix, c->bary_off, c->own_px, c->own_np, c->bary_sh, c->bary_keys, c->bary_cnt);
-        const unsigned gv = (unsigned)std::min<int64_t>((nb + 7) / 8, (int64_t)c->num_sms * 64);
-        k_bary_vec<<<gv, 256, 0, s>>>(N, nb, c->bary_keys, c->offsets, c->rec_radec, c->rec_shear, c->ring_lat,
-                                      c->bary_geo, c->bary_vec);
+        const unsigned gw = (unsigned)std::min<int64_t>((c->n_gal + 255) / 256, (int64_t)c->num_sms * 32);
+        k_bary_wr<<<gw, 256, 0, s>>>(c->n_gal, c->rec_radec, c->rec_shear, c->bary_wr);
+        const unsigned gv = (unsigned)std::min<int64_t>((nb + 127) / 128, (int64_t)c->num_sms * 32);
+        k_bary_vec<<<gv, 128, 0, s>>>(N, nb, c->bary_keys, c->offsets, c->bary_wr, c->ring_lat, c->bary_geo,
+                                      c->bary_vec);
     }
     if ((st = check_cuda(c, cudaGetLastError(), "barycentre records")) != SMART_OK) return st;
     c->bary_version = c->catalog_version;

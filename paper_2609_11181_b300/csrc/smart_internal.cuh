@@ -361,6 +361,8 @@ struct smart_ctx {
     int32_t *bary_cnt = nullptr;                     // galaxies of the record's pixel
     double *bary_vec = nullptr;                      // float64 unit vector, 3 per record
     int64_t n_bary = 0, cap_bary = 0;
+    double *bary_wr = nullptr;                       // w r of every galaxy (build scratch)
+    int64_t cap_bary_wr = 0;
     int32_t *raw_m = nullptr;                        // member records per target
     int64_t cap_raw_m = 0;
 
