@@ -304,6 +304,47 @@ def map_barycentre(centres, nside_bin, ra, dec, e1, e2, w, kind, theta_ap, xc=0.
                                     kind, theta_ap, xc), theta_ap)
 
 
+# --------------------------------------------------------------------------
+# averaged normalisation (Sect. 2.4): each bin pixel's shear is normalised by
+# its own weight and multiplied by the pixel area (the analogue of the
+# convergence-based map, Sect. 5.3 step 2); no aperture density.
+#   M_E = sum_p Q (G+_p / W_p) A_pix,  sigma^2 = 1/2 sum_p Q^2 S2_p (A_pix / W_p)^2
+# For galaxies each one carries w A_pix / W of its bin pixel.
+# --------------------------------------------------------------------------
+def _averaged(sums: dict) -> dict:
+    out = dict(sums)
+    out.update(ME=np.asarray(sums["SE"], np.float64), MB=np.asarray(sums["SB"], np.float64),
+               VAR=0.5 * np.asarray(sums["SV"], np.float64))
+    return out
+
+
+def _avg_scale(nside_bin: int, W) -> np.ndarray:
+    W = np.asarray(W, np.float64)
+    apix = 4.0 * np.pi / (12.0 * nside_bin * nside_bin)
+    return np.divide(apix, W, out=np.zeros_like(W), where=W > 0)
+
+
+def map_pixels_averaged(centres, nside_bin, G1, G2, W, S2, n_p, kind, theta_ap, xc=0.15):
+    f = _avg_scale(nside_bin, W)
+    G1, G2, S2 = (np.asarray(a, np.float64) for a in (G1, G2, S2))
+    return _averaged(aperture_pixels(centres, nside_bin, G1 * f, G2 * f, W, S2 * f * f, n_p, kind, theta_ap, xc))
+
+
+def map_galaxies_averaged(centres, nside_bin, ra, dec, e1, e2, w, kind, theta_ap, xc=0.15):
+    b = bin_catalog(nside_bin, ra, dec, e1, e2, w)
+    f = _avg_scale(nside_bin, b["W"])[b["pix"]]
+    return _averaged(aperture_galaxies(centres, ra, dec, e1, e2, np.asarray(w, np.float64) * f, kind, theta_ap, xc))
+
+
+def map_barycentre_averaged(centres, nside_bin, ra, dec, e1, e2, w, kind, theta_ap, xc=0.15):
+    b = bin_catalog(nside_bin, ra, dec, e1, e2, w)
+    bc = barycentres(nside_bin, ra, dec, w, b)
+    p = bc["pix"]
+    f = _avg_scale(nside_bin, b["W"][p])
+    return _averaged(aperture_points(centres, bc["vec"], b["G1"][p] * f, b["G2"][p] * f, b["W"][p],
+                                     b["S2"][p] * f * f, b["n"][p], kind, theta_ap, xc))
+
+
 def rms_rel(a, b) -> float:
     """rms(a - b) / rms(b): the map parity statistic."""
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)

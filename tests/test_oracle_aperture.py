@@ -387,3 +387,57 @@ def test_barycentre_is_the_weighted_mean_direction():
     bc = oracle.barycentres(nside, ra, dec, w, b)
     want = (3.0 * pts[0] + pts[1]) / np.linalg.norm(3.0 * pts[0] + pts[1])
     np.testing.assert_allclose(bc["vec"][0], want, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# averaged normalisation (Sect. 2.4)
+# --------------------------------------------------------------------------
+def test_averaged_equals_summed_times_pixel_area_ratio_for_equal_weights():
+    # when every bin pixel carries the same weight W0, the averaged map is the
+    # summed map times (members x pixel area) / aperture area, exactly
+    nside = 64
+    npix = 12 * nside * nside
+    rng = np.random.default_rng(21)
+    G1, G2 = rng.normal(0, 1, npix), rng.normal(0, 1, npix)
+    W = np.full(npix, 7.0)
+    S2 = rng.uniform(1, 2, npix)
+    n_p = np.full(npix, 7, np.int64)
+    tg = oracle.pix2vec(32, np.arange(0, 12 * 32 * 32, 97))
+    th = 3.0 * np.pi / 180
+    s = oracle.map_pixels(tg, nside, G1, G2, W, S2, n_p, 2, th)
+    a = oracle.map_pixels_averaged(tg, nside, G1, G2, W, S2, n_p, 2, th)
+    apix = 4 * np.pi / npix
+    area = 2 * np.pi * (1 - np.cos(th))
+    ratio = s["NPIX"] * apix / area
+    np.testing.assert_allclose(a["ME"], s["ME"] * ratio, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a["MB"], s["MB"] * ratio, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(a["VAR"], s["VAR"] * ratio ** 2, rtol=1e-12, atol=1e-18)
+
+
+def test_averaged_map_of_a_smooth_field_approaches_the_integral():
+    # averaged = the pixel discretisation of int gamma_+ Q dA: for a noiseless
+    # isolated SIS the polynomial-filter map tends to the closed form of the
+    # flat limit, 4 theta_E / (5 theta_ap), as pixels shrink
+    nside = 1024
+    te = 0.5 * ARCMIN
+    th = 30.0 * ARCMIN
+    ra0, dec0 = 0.0, 0.0
+    tgt = oracle.radec2vec([ra0], [dec0])
+    pix = oracle.query_disc(nside, tgt[0], th)
+    v = oracle.pix2vec(nside, pix)
+    # gamma_t = theta_E / (2 theta), tangential about the halo at the target
+    x, y, z = v[:, 0], v[:, 1], v[:, 2]
+    ra = np.arctan2(y, x)
+    dec = np.arcsin(z)
+    theta = 2 * np.arcsin(np.linalg.norm(v - tgt[0], axis=1) / 2)
+    gt = np.where(theta > te, te / (2 * np.maximum(theta, 1e-300)), 0.5)
+    # bearing of the halo (at ra0, dec0) from each pixel, from North through East
+    b = np.arctan2(np.sin(-ra) * np.cos(0.0), np.cos(dec) * np.sin(0.0) - np.sin(dec) * np.cos(0.0) * np.cos(-ra))
+    g1 = np.zeros(12 * nside * nside)
+    g2 = np.zeros(12 * nside * nside)
+    g1[pix] = gt * np.cos(2 * b)
+    g2[pix] = -gt * np.sin(2 * b)
+    W = np.ones(12 * nside * nside)
+    a = oracle.map_pixels_averaged(tgt, nside, g1, g2, W, np.zeros_like(W), np.ones(W.size, np.int64), 1, th)
+    assert abs(a["ME"][0] - 4 * te / (5 * th)) < 0.02 * 4 * te / (5 * th)
+    assert abs(a["MB"][0]) < 1e-3 * 4 * te / (5 * th)
