@@ -173,6 +173,20 @@ smart_status smart_map_pixel(smart_ctx *ctx, const smart_maps *out);
  */
 smart_status smart_map_barycentre(smart_ctx *ctx, const smart_maps *out);
 
+/*
+ * Normalisation of the maps of a context (Sect. 2.4).
+ * SMART_NORM_SUMMED (default): M = A S / sum_w with A the aperture area,
+ *   sigma^2 = A^2 V / (2 sum_w^2) (the paper's default form).
+ * SMART_NORM_AVERAGED: each bin pixel's shear is normalised by that pixel's
+ *   own weight W and multiplied by the pixel area A_pix (galaxies carry
+ *   w A_pix / W of their bin pixel): M = sum Q gamma+ A_pix / W,
+ *   sigma^2 = 1/2 sum Q^2 S2 (A_pix / W)^2; sum_w stays the aperture's weight
+ *   and must be requested.  Applies to smart_map_pixel, smart_map_barycentre
+ *   and smart_map_bruteforce; batches reject contexts in this mode.
+ */
+typedef enum { SMART_NORM_SUMMED = 0, SMART_NORM_AVERAGED = 1 } smart_norm;
+smart_status smart_set_normalisation(smart_ctx *ctx, int mode);
+
 
 /* ---- batched pixel-based maps ----------------------------------------- */
 

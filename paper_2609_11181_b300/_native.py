@@ -50,6 +50,7 @@ SIGNATURES = {
     "smart_map_bruteforce": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
     "smart_map_pixel": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
     "smart_map_barycentre": (_I32, [_VP, ctypes.POINTER(SmartMaps)]),
+    "smart_set_normalisation": (_I32, [_VP, _I32]),
     "smart_ang2pix": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP]),
     "smart_pix2vec": (_I32, [_I32, _VP, _I64, _VP, _VP]),
     "smart_chord2": (_D, [_D]),

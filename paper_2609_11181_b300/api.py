@@ -167,6 +167,12 @@ class Context:
         self._check(self._lib.smart_map_pixel(self._h, ctypes.byref(m)), "smart_map_pixel")
         return out
 
+    def set_normalisation(self, mode: str):
+        """'summed' (default: M = A S / sum_w) or 'averaged' (each bin pixel's shear over its own weight, times
+        the pixel area)."""
+        m = {"summed": 0, "averaged": 1}[mode]
+        self._check(self._lib.smart_set_normalisation(self._h, m), "smart_set_normalisation")
+
     def map_barycentre(self, out: dict | None = None) -> dict:
         """Pixel-based map with the bin pixels at their galaxies' barycentres (needs bin_galaxies)."""
         out, m = self._out(out)

@@ -214,6 +214,11 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
             smart_batch_destroy(b);
             return SMART_E_ARG;
         }
+        if (ctxs[m]->norm != SMART_NORM_SUMMED) {
+            bfail(b, SMART_E_ARG, "batches use the summed normalisation");
+            smart_batch_destroy(b);
+            return SMART_E_ARG;
+        }
     }
     b->ctxs.assign(ctxs, ctxs + n_maps);
     b->args.resize(n_maps);

@@ -546,6 +546,13 @@ static smart_status map_records(smart_ctx *c, const smart_maps *out, bool bary) 
     cudaMemsetAsync(c->d_fp64_count, 0, sizeof(unsigned long long), c->stream);
     cudaMemsetAsync(c->d_band_count, 0, sizeof(unsigned long long), c->stream);
     if (n == 0) return SMART_OK;
+    const bool averaged = c->norm == SMART_NORM_AVERAGED;
+    if (averaged) {
+        // galaxy records take the W of their bin pixel, pixel records their own
+        st = bary ? averaged_record_input(c, c->bary_sh, nullptr, nullptr, c->n_bary, &a.shear)
+                  : averaged_record_input(c, c->rec_shear, c->keys, c->own_px, c->n_gal, &a.shear);
+        if (st != SMART_OK) return st;
+    }
     const unsigned blocks = (unsigned)((a.n_tiles + GW - 1) / GW);
     const bool poly = c->filter_kind == SMART_FILTER_POLY;
     if (bary) {
@@ -573,7 +580,9 @@ static smart_status map_records(smart_ctx *c, const smart_maps *out, bool bary) 
         KernelTimer timer(c, SMART_KT_GALAXY_FINALISE);
         k_galaxy_finalise<<<fb, 256, 0, c->stream>>>(a, bary ? c->raw_m : nullptr);
     }
-    return check_cuda(c, cudaGetLastError(), bary ? "barycentre launches" : "brute-force launches");
+    st = check_cuda(c, cudaGetLastError(), bary ? "barycentre launches" : "brute-force launches");
+    if (st == SMART_OK && averaged) st = averaged_rescale(c, out);
+    return st;
 }
 
 extern "C" smart_status smart_map_bruteforce(smart_ctx *c, const smart_maps *out) {

@@ -474,6 +474,8 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     cudaMemsetAsync(c->d_work, 0, sizeof(int), c->stream);
     st = launch_count_prefix(c);
     if (st != SMART_OK || a.n == 0) return st;
+    const bool averaged = c->norm == SMART_NORM_AVERAGED;
+    if (averaged && (st = averaged_pixel_input(c, a.PX, &a.PX)) != SMART_OK) return st;
     if (a.n_gen < a.n) {
         const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * 4);
         KernelTimer timer(c, SMART_KT_PIXEL_TOEPLITZ);
@@ -489,5 +491,6 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
         else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a);
         st = check_cuda(c, cudaGetLastError(), "k_pixel_general launch");
     }
+    if (st == SMART_OK && averaged) st = averaged_rescale(c, out);
     return st;
 }

@@ -89,7 +89,7 @@ extern "C" void smart_destroy(smart_ctx *c) {
                     c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
                     c->toe_ring, c->gen_list, c->gal_tiles, c->raw, c->band, c->d_band_count,
                     c->d_status, c->d_fp64_count, c->bary_off, c->bary_geo, c->bary_sh, c->bary_keys,
-                    c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m};
+                    c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m, c->avg_buf};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

@@ -361,6 +361,9 @@ struct smart_ctx {
     int32_t *bary_cnt = nullptr;                     // galaxies of the record's pixel
     double *bary_vec = nullptr;                      // float64 unit vector, 3 per record
     int64_t n_bary = 0, cap_bary = 0;
+    int norm = SMART_NORM_SUMMED;                    // normalisation of the maps (Sect. 2.4)
+    float4 *avg_buf = nullptr;                       // inputs scaled for the averaged form
+    int64_t cap_avg = 0;
     double *bary_wr = nullptr;                       // w r of every galaxy (build scratch)
     int64_t cap_bary_wr = 0;
     int32_t *raw_m = nullptr;                        // member records per target
@@ -397,6 +400,13 @@ smart_status build_tiles_log2(smart_ctx *ctx, int log2_slots, int64_t **tiles, i
 
 // context.cu
 smart_status ensure_own_binned_map(smart_ctx *ctx);
+
+// normalise.cu (averaged normalisation): scaled inputs in ctx->avg_buf, and
+// the rescale of the summed-form outputs
+smart_status averaged_pixel_input(smart_ctx *c, const float4 *px, const float4 **out);
+smart_status averaged_record_input(smart_ctx *c, const float4 *sh, const uint32_t *keys, const float4 *px, int64_t n,
+                                   const float4 **out);
+smart_status averaged_rescale(smart_ctx *c, const smart_maps *out);
 
 // Brackets one kernel launch with events on the context stream while timing
 // is enabled (smart_timing_enable); does nothing otherwise.
