@@ -54,13 +54,18 @@ typedef enum {
 
 typedef enum {
     SMART_FILTER_POLY = 1,      /* Schneider (1996): Q = 6/pi x^2 (1 - x^2) / theta_ap^2      */
-    SMART_FILTER_SCHIRMER = 2   /* Schirmer et al. (2007): Q = tanh(x/xc)/(x/xc) /
+    SMART_FILTER_SCHIRMER = 2,  /* Schirmer et al. (2007): Q = tanh(x/xc)/(x/xc) /
                                    (1 + e^(6-150x) + e^(-47+50x)) / theta_ap^2               */
+    SMART_FILTER_JARVIS = 3     /* Jarvis et al. (2004), Gaussian-type, scale s = xc:
+                                   Q = (x/s)^2 exp(-x^2 / (2 s^2)) / (4 pi s^2) / theta_ap^2,
+                                   truncated at x = 1 (the aperture radius)                  */
 } smart_filter_kind;
 
 typedef struct {
     int kind;                   /* smart_filter_kind                          */
-    double xc;                  /* Schirmer core, default 0.15; ignored else  */
+    double xc;                  /* Schirmer core (default 0.15) or Jarvis scale
+                                   in units of theta_ap (default 0.25); ignored
+                                   by the polynomial filter                   */
 } smart_filter;
 
 /* Output buffers, one entry per target pixel (device pointers; any may be

@@ -281,6 +281,11 @@ double orc_filter_q(int kind, double xc, double x)
         double th = (r == 0.0) ? 1.0 : tanh(r) / r;
         return th / (1.0 + exp(6.0 - 150.0 * x) + exp(-47.0 + 50.0 * x));
     }
+    if (kind == 3) {
+        /* Jarvis et al. (2004), Gaussian-type, scale s = xc (in theta_ap units) */
+        double s2 = xc * xc;
+        return x * x / s2 * exp(-0.5 * x * x / s2) / (4.0 * ORC_PI * s2);
+    }
     return 0.0;
 }
 

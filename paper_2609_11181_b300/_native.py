@@ -25,6 +25,7 @@ MLP_FP32 = 1
 
 FILTER_POLY = 1
 FILTER_SCHIRMER = 2
+FILTER_JARVIS = 3
 
 
 class SmartFilter(ctypes.Structure):

@@ -64,10 +64,12 @@ def pix2vec(nside: int, pix: torch.Tensor) -> torch.Tensor:
 class Context:
     """One aperture-mass problem: output grid, filter, aperture, bin grid."""
 
-    def __init__(self, nside_out: int, theta_ap_arcmin: float, filter: str = "poly", xc: float = 0.15,
+    def __init__(self, nside_out: int, theta_ap_arcmin: float, filter: str = "poly", xc: float | None = None,
                  nside_bin: int | None = None, stream: torch.cuda.Stream | None = None):
         self._lib = N.load()
-        kind = {"poly": N.FILTER_POLY, "schirmer": N.FILTER_SCHIRMER}[filter]
+        kind = {"poly": N.FILTER_POLY, "schirmer": N.FILTER_SCHIRMER, "jarvis": N.FILTER_JARVIS}[filter]
+        if xc is None:
+            xc = 0.25 if filter == "jarvis" else 0.15
         f = N.SmartFilter(kind, float(xc))
         h = ctypes.c_void_p()
         self._stream = stream

@@ -90,8 +90,10 @@ __device__ __forceinline__ float qtab_eval(const float4 *tab, float s2, float sc
     return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
 }
 
-// Q(d) from the chord^2.  Polynomial filter in closed form; the Schirmer
-// filter through its cubic table (tab: a shared-memory or global copy).
+// Q(d) from the chord^2.  Polynomial filter in closed form; the tabulated
+// filters (Schirmer, Jarvis) through their cubic table (tab: a shared-memory
+// or global copy).  KIND == SMART_FILTER_SCHIRMER stands for every tabulated
+// filter: the table, not the template, carries the filter.
 template <int KIND>
 __device__ __forceinline__ float filter_Q(const FilterArgs &f, const float4 *tab, float s2) {
     if (KIND == SMART_FILTER_POLY) {

@@ -277,25 +277,34 @@ __device__ double schirmer_q(double x, double xc, double *dq) {
     return th * g;
 }
 
-// Q and dQ/ds at chord s
-__device__ double schirmer_Q_of_chord(double s, double xc, double theta_ap, double *dQ) {
+// Jarvis et al. (2004) Gaussian-type filter with scale s (units of theta_ap):
+// q = (x/s)^2 exp(-x^2 / (2 s^2)) / (4 pi s^2), and dq/dx
+__device__ double jarvis_q(double x, double s, double *dq) {
+    const double s2 = s * s;
+    const double e = exp(-0.5 * x * x / s2) / (4.0 * SMART_PI * s2);
+    *dq = e * (2.0 * x / s2 - x * x * x / (s2 * s2));
+    return e * x * x / s2;
+}
+
+// Q and dQ/ds at chord s of a tabulated filter (Schirmer or Jarvis)
+__device__ double table_Q_of_chord(int kind, double s, double xc, double theta_ap, double *dQ) {
     const double half = 0.5 * s;
     const double d = 2.0 * asin(half);
     const double dd = 1.0 / sqrt(1.0 - half * half);          // d d / d s
     double dq;
-    const double q = schirmer_q(d / theta_ap, xc, &dq);
+    const double q = kind == SMART_FILTER_JARVIS ? jarvis_q(d / theta_ap, xc, &dq) : schirmer_q(d / theta_ap, xc, &dq);
     const double n = 1.0 / (theta_ap * theta_ap);
     *dQ = n * dq * dd / theta_ap;
     return n * q;
 }
 
-__global__ void k_filter_table(double xc, double theta_ap, double sap, float4 *__restrict__ tab) {
+__global__ void k_filter_table(int kind, double xc, double theta_ap, double sap, float4 *__restrict__ tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= QTAB_BINS) return;
     const double h = sap / QTAB_BINS;
     double d0, d1;
-    const double q0 = schirmer_Q_of_chord(i * h, xc, theta_ap, &d0);
-    const double q1 = schirmer_Q_of_chord((i + 1) * h, xc, theta_ap, &d1);
+    const double q0 = table_Q_of_chord(kind, i * h, xc, theta_ap, &d0);
+    const double q1 = table_Q_of_chord(kind, (i + 1) * h, xc, theta_ap, &d1);
     d0 *= h;
     d1 *= h;
     // Hermite cubic on t in [0, 1]: q0 + d0 t + c2 t^2 + c3 t^3
@@ -307,7 +316,8 @@ __global__ void k_filter_table(double xc, double theta_ap, double sap, float4 *_
 smart_status ensure_filter_table(smart_ctx *c) {
     if (c->filter_kind == SMART_FILTER_POLY || c->qtab) return SMART_OK;
     if (cudaMalloc(&c->qtab, QTAB_BINS * sizeof(float4)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(filter table) failed");
-    k_filter_table<<<(QTAB_BINS + 127) / 128, 128, 0, c->stream>>>(c->xc, c->theta_ap, sqrt(c->T), c->qtab);
+    k_filter_table<<<(QTAB_BINS + 127) / 128, 128, 0, c->stream>>>(c->filter_kind, c->xc, c->theta_ap, sqrt(c->T),
+                                                                  c->qtab);
     return check_cuda(c, cudaGetLastError(), "k_filter_table");
 }
 

@@ -51,15 +51,16 @@ extern "C" smart_status smart_create(int nside_out, const smart_filter *filter, 
     if (!out) return SMART_E_ARG;
     *out = nullptr;
     if (!nside_ok(nside_out) || !nside_ok(nside_bin) || !filter) return SMART_E_ARG;
-    if (filter->kind != SMART_FILTER_POLY && filter->kind != SMART_FILTER_SCHIRMER) return SMART_E_ARG;
-    if (filter->kind == SMART_FILTER_SCHIRMER && !(filter->xc > 0.0 && filter->xc < 10.0)) return SMART_E_ARG;
+    if (filter->kind != SMART_FILTER_POLY && filter->kind != SMART_FILTER_SCHIRMER && filter->kind != SMART_FILTER_JARVIS)
+        return SMART_E_ARG;
+    if (filter->kind != SMART_FILTER_POLY && !(filter->xc > 0.0 && filter->xc < 10.0)) return SMART_E_ARG;
     if (!(theta_ap_arcmin > 0.0) || !(theta_ap_arcmin <= 3600.0)) return SMART_E_ARG;
     smart_ctx *c = new (std::nothrow) smart_ctx();
     if (!c) return SMART_E_NOMEM;
     c->nside_out = nside_out;
     c->nside_bin = nside_bin;
     c->filter_kind = filter->kind;
-    c->xc = filter->kind == SMART_FILTER_SCHIRMER ? filter->xc : 0.15;
+    c->xc = filter->kind == SMART_FILTER_POLY ? 0.15 : filter->xc;
     c->theta_ap = theta_ap_arcmin * SMART_PI / 10800.0;
     c->T = smart_chord2(theta_ap_arcmin);
     c->area = 2.0 * SMART_PI * (0.5 * c->T);     // 2 pi (1 - cos theta_ap) = pi T

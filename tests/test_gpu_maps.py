@@ -143,3 +143,15 @@ def test_packed_and_soa_inputs_agree(cuda_device):
         assert torch.equal(m1[k], m2[k]), k
     for k, x in zip(("G1", "G2", "W", "S2", "n"), G):
         assert torch.equal(back[k], x), k
+
+
+@pytest.mark.parametrize("ra0,dec0,no,nb", [(75.0, 5.0, 256, 512), (20.0, 70.0, 256, 256)])
+def test_jarvis_filter_maps(cuda_device, ra0, dec0, no, nb):
+    """The Gaussian-type filter of Jarvis et al. (2004), scale theta_ap / 4,
+    through the tabulated-filter path of both map kernels."""
+    cat = catalog(int(ra0 + dec0) + 900, 60_000, ra0, dec0, 3.5, nhalo=5, w_range=(0.5, 1.5), clumped=True)
+    tg = cap_targets(no, ra0, dec0, 3.0)
+    ctx, bf, px, _ = _gal_run(cuda_device, cat, tg, no, nb, 24.0, "jarvis", xc=0.25)
+    rbf, rpx = _oracle_maps(cat, tg, no, nb, 24.0, 3, xc=0.25)
+    _check(bf, rbf, "brute")
+    _check(px, rpx, "pixel")

@@ -441,3 +441,24 @@ def test_averaged_map_of_a_smooth_field_approaches_the_integral():
     a = oracle.map_pixels_averaged(tgt, nside, g1, g2, W, np.zeros_like(W), np.ones(W.size, np.int64), 1, th)
     assert abs(a["ME"][0] - 4 * te / (5 * th)) < 0.02 * 4 * te / (5 * th)
     assert abs(a["MB"][0]) < 1e-3 * 4 * te / (5 * th)
+
+
+# --------------------------------------------------------------------------
+# Jarvis et al. (2004) filter
+# --------------------------------------------------------------------------
+def _u_jarvis(x, s):
+    """The compensated U of the Gaussian-type filter (theta_ap = 1, scale s)."""
+    return (1.0 - x * x / (2 * s * s)) * np.exp(-x * x / (2 * s * s)) / (2 * np.pi * s * s)
+
+
+def test_jarvis_q_follows_from_its_compensated_u():
+    from scipy.integrate import quad
+    s = 0.25
+    # U is compensated over the whole plane: int_0^inf x U dx = 0
+    comp, _ = quad(lambda t: t * _u_jarvis(t, s), 0, 40 * s, limit=200)
+    assert abs(comp) < 1e-12
+    # Eq. 5: Q = (2 / x^2) int_0^x x' U dx' - U
+    for x in (0.05, 0.1, 0.25, 0.4, 0.7, 1.0):
+        inner, _ = quad(lambda t: t * _u_jarvis(t, s), 0, x, epsabs=1e-14, epsrel=1e-12)
+        q_from_u = 2.0 / (x * x) * inner - _u_jarvis(x, s)
+        assert abs(oracle.filter_q(3, x, s) - q_from_u) < 1e-10 * max(1.0, abs(q_from_u))
