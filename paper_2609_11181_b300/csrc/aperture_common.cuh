@@ -104,8 +104,9 @@ __device__ __forceinline__ float filter_Q(const FilterArgs &f, const float4 *tab
     }
 }
 
-// sin u and sin^2(u/2): 2-term series for |u| <= 0.05 (rel. error < 1e-10),
-// 4-term for |u| <= 0.45 (< 2e-9), library sincos beyond
+// sin u and sin^2(u/2): 2-term series for |u| <= 0.05 (relative truncation
+// below 6e-8, under float32 rounding), 4-term for |u| <= 0.45 (below 5e-9),
+// longer series beyond
 __device__ __forceinline__ void sin_hav_narrow(float u, float &sinu, float &h) {
     const float u2 = u * u;
     sinu = u * fmaf(u2, -1.0f / 6.0f, 1.0f);

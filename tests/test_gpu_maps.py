@@ -155,3 +155,34 @@ def test_jarvis_filter_maps(cuda_device, ra0, dec0, no, nb):
     rbf, rpx = _oracle_maps(cat, tg, no, nb, 24.0, 3, xc=0.25)
     _check(bf, rbf, "brute")
     _check(px, rpx, "pixel")
+
+
+def test_pixel_map_at_nside_8192(cuda_device):
+    """The largest grid (12 x 8192^2 = 8.05e8 pixels, full-sky arrays of 16 GB):
+    a cap straddling the polar / equatorial boundary (dec 41.8), so both pixel
+    kernels run, Schirmer 2'."""
+    nside = 8192
+    npix = 12 * nside * nside
+    c = oracle.radec2vec([123.0], [41.8])[0]
+    src = oracle.query_disc(nside, c, math.radians(0.35))
+    rng = np.random.default_rng(8192)
+    G1, G2, W, S2 = (np.zeros(npix, np.float32) for _ in range(4))
+    n_p = np.zeros(npix, np.int32)
+    n = rng.poisson(6.0, src.size).astype(np.int32)
+    w = n * rng.uniform(0.5, 1.5, src.size)
+    G1[src] = w * rng.normal(0.0, 0.3, src.size)
+    G2[src] = w * rng.normal(0.0, 0.3, src.size)
+    W[src] = w
+    S2[src] = w * 0.3
+    n_p[src] = n
+    tg = np.sort(oracle.query_disc(nside, c, math.radians(0.25)))
+    ctx = api.Context(nside, 2.0, "schirmer", nside_bin=nside)
+    ctx.set_targets(torch.from_numpy(tg).to(cuda_device))
+    ctx.set_binned(*(torch.from_numpy(x).to(cuda_device) for x in (G1, G2, W, S2, n_p)))
+    got = ctx.map_pixel()
+    ctx.sync(120)
+    gen = ctx.general_targets().numel()
+    assert 0 < gen < tg.size
+    ref = oracle.finalise(oracle.aperture_pixels_f32(oracle.pix2vec(nside, tg), nside, G1, G2, W, S2, n_p, 2,
+                                                     2.0 * ARCMIN), 2.0 * ARCMIN)
+    _check(got, ref, "nside 8192")

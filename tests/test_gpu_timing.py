@@ -56,3 +56,26 @@ def test_bruteforce_and_binning_timing(cuda_device):
                  "galaxy_finalise"):
         n, ms = ctx.timing_read(name)
         assert n == 1 and ms >= 0.0, name
+
+
+def test_sync_deadline_times_out_and_context_stays_usable(cuda_device):
+    # a stream kept busy by several maps: a wait with a tiny deadline gives up
+    # with SMART_E_TIMEOUT; the work completes and a later wait succeeds
+    from paper_2609_11181_b300 import workloads
+    wl = workloads.pixel_workload(cuda_device, api.pix2vec, nside=1024, area_deg2=2000.0, theta_ap=30.0,
+                                  filt="schirmer", dec0=50.0)
+    ctx = api.Context(wl.nside, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside)
+    ctx.set_targets(wl.targets)
+    ctx.set_binned(wl.G1, wl.G2, wl.W, wl.S2, wl.n)
+    ref = ctx.map_pixel()
+    ctx.sync(60)
+    ref = {k: v.clone() for k, v in ref.items()}
+    out = None
+    for _ in range(8):
+        out = ctx.map_pixel()
+    with pytest.raises(api.SmartError) as err:
+        ctx.sync(1e-6)
+    assert "TIMEOUT" in str(err.value)
+    ctx.sync(60)
+    for k in ref:
+        assert torch.equal(out[k], ref[k]), k
