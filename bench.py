@@ -29,6 +29,7 @@ import shutil
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -61,11 +62,12 @@ class Clocks:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        out_dir = os.environ.get("SMART_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"smart_clocks_rank{gpu_index}_{os.getpid()}.csv")
         exe = shutil.which("nvidia-smi")
         if exe is None:
             return
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        os.makedirs(out_dir, exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -566,7 +568,7 @@ LEARNED = dict(area_deg2=300.0, n_gal=20_000_000, nside=2048, theta_ap=10.0, fil
 def run_native_learned(args, world, rank):
     """Learned residual correction: maps of seeded 300 deg^2 caps (2e7 galaxies,
     half clumped) at NSIDE 2048, Schirmer 10'; the network is trained on the
-    training maps' brute-force minus pixel-based residuals and judged against
+    training maps' brute-force minus pixel-based residuals and compared with
     brute force on held-out maps."""
     from paper_2609_11181_b300 import synth
     dev = torch.device("cuda", torch.cuda.current_device())
