@@ -16,9 +16,11 @@
  *  - Array arguments are DEVICE pointers owned by the caller unless a
  *    parameter says "host".  The caller keeps inputs alive until
  *    smart_sync() returns.
- *  - Every call is asynchronous on the context's CUDA stream (the stream
- *    given to smart_create, 0 = legacy default stream) and returns at once;
- *    only smart_sync() blocks.
+ *  - Calls run asynchronously on the context's CUDA stream (the stream
+ *    given to smart_create, 0 = legacy default stream) and return at once,
+ *    unless their description says that they wait (smart_sync with a
+ *    deadline; smart_bin_galaxies and the table builders read one value
+ *    back; the timing and MLP state calls copy to the host).
  *  - The library owns only its internal scratch (sorted catalogue, offsets,
  *    ring tables, binned maps it made itself) and frees it in
  *    smart_destroy().
@@ -123,7 +125,9 @@ smart_status smart_set_targets(smart_ctx *ctx, const int64_t *ring_pix, int64_t 
  *   n = count
  * in float32, accumulated in sorted order.  ra/dec: f64 degrees; e1, e2,
  * w: f32; all device pointers of n entries.  w may be NULL (all weights 1).
- * Replaces any binned map given earlier with smart_set_binned.
+ * Replaces any binned map given earlier with smart_set_binned.  Waits for
+ * the stream before returning: galaxies with non-finite ra/dec or
+ * |dec| > 90 make it return SMART_E_ARG (the catalogue is then unusable).
  */
 smart_status smart_bin_galaxies(smart_ctx *ctx, const double *ra_deg,
                                 const double *dec_deg, const float *e1,
