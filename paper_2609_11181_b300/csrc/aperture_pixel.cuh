@@ -123,17 +123,16 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
         // the bin pixel's data is loaded one iteration ahead (the load of the
         // last pixel is repeated, never past the run)
         float4 gn = __ldg(a.PX + pbeg);
-        int nnext = __ldg(a.NP + pbeg);
+        // the strict members of a run are contiguous (s^2 grows with |u|): their
+        // number and the last one give the galaxy count from the count prefix
+        int nrun = 0, last = -1;
         // branch-free body (non-members add zeros), so that consecutive pairs
         // can interleave; guard-band pairs take the rare branch
 #pragma unroll 2
         for (int i = 0; i < cnt; ++i) {
             const int p = pbeg + i;
             const float4 g = gn;
-            const int np = nnext;
-            const int pn = min(p + 1, plast);
-            gn = __ldg(a.PX + pn);
-            nnext = __ldg(a.NP + pn);
+            gn = __ldg(a.PX + min(p + 1, plast));
             const float u = fmaf(kf, R.dphi, u0);
             kf += 1.0f;
             float sinu, h;
@@ -162,8 +161,12 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
             pv = fmaf(in ? Q * Q : 0.f, g.z, pv);
             pw += in ? g.w : 0.f;
-            nn += in ? np : 0;
-            nm += in ? 1 : 0;
+            nrun += in ? 1 : 0;
+            last = in ? i : last;
+        }
+        if (nrun > 0) {
+            nn += __ldg(a.NPRE + pbeg + last + 1) - __ldg(a.NPRE + pbeg + last + 1 - nrun);
+            nm += nrun;
         }
     }
     if (ndef > 2) {
