@@ -154,6 +154,7 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
             const int cnt = BARY ? __ldg(ba.cnt + g) : 1;
             float A, B, C, D, frg;
             gal_setup(R, geo, A, B, C, D, frg);
+            unsigned band = 0;       // targets for which this galaxy lies in the guard band
 #pragma unroll
             for (int r = 0; r < GT; ++r) {
                 const float u = gal_u(R, kg, frg, Xi[r], Xf[r]);
@@ -162,16 +163,7 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
                 else sin_hav_wide(u, sinu, h);
                 const float s2 = fmaf(B, h, A);
                 const bool in = on[r] && s2 < a.Tlo;
-                if (on[r] && !(s2 < a.Tlo) && s2 <= a.Thi) {
-                    const unsigned long long slot = atomicAdd(a.band_count, 1ull);
-                    if (slot < (unsigned long long)a.band_cap) {
-                        BandPair bp;
-                        bp.target = tb + r;
-                        bp.galaxy = g;
-                        bp.entry = e;
-                        reinterpret_cast<BandPair *>(a.band)[slot] = bp;
-                    }
-                }
+                band |= (on[r] && !(s2 < a.Tlo) && s2 <= a.Thi) ? (1u << r) : 0u;
                 const float x = R.mrho0 * sinu;
                 const float y = fmaf(D, h, C);
                 const float xx = x * x;
@@ -186,6 +178,19 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
                 pw[r] += in ? sh.z : 0.f;
                 nn[r] += in ? cnt : 0;
                 if (BARY) nm[r] += in ? 1 : 0;
+            }
+            if (band) {              // rare: one branch per galaxy, not per pair
+                for (int r = 0; r < GT; ++r) {
+                    if (!(band & (1u << r))) continue;
+                    const unsigned long long slot = atomicAdd(a.band_count, 1ull);
+                    if (slot < (unsigned long long)a.band_cap) {
+                        BandPair bp;
+                        bp.target = tb + r;
+                        bp.galaxy = g;
+                        bp.entry = e;
+                        reinterpret_cast<BandPair *>(a.band)[slot] = bp;
+                    }
+                }
             }
         }
     }
