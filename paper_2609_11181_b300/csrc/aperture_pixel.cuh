@@ -90,9 +90,9 @@ __device__ __forceinline__ void pixel_pair(const MapArgs &a, const RingPair &R, 
 // pixel-mode general pair loop for one target and one ring pair; MODE picks
 // the sine series by the largest |u| of the ring pair (0: <= 0.05 rad,
 // 1: <= 0.45 rad, 2: |u| <= pi).  Pairs inside the float32 guard band are
-// set aside (a ring segment crosses the band edge at most twice) and
-// decided in float64 after the loop, which keeps the float64 code out of
-// the hot loop.
+// only counted in the loop, which keeps its body free of branches; when
+// there are any (rarely), the window is scanned again and they are decided
+// in float64 after the loop.
 template <int KIND, int MODE>
 __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
                                                 const LatticeDiv &ld, int64_t pix, const float4 *qtab, float &pe,
@@ -108,8 +108,7 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
     int kk0 = Xi + kl;
     kk0 += kk0 < 0 ? R.nr : (kk0 >= R.nr ? -R.nr : 0);
     const float u0 = fr * R.dphi;
-    int def0 = -1, def1 = -1, ndef = 0;
-    float ud0 = 0.f, ud1 = 0.f;
+    int nband = 0;          // pairs inside the float32 guard band
     // the window's pixels are [kk0, nr) then [0, rest) when it wraps
     const int len = kh - kl + 1;
     const int n1 = min(len, R.nr - kk0);
@@ -139,16 +138,7 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             sin_hav<MODE>(u, sinu, h);
             const float s2 = fmaf(R.B, h, R.A);
             const bool in = s2 < a.Tlo;
-            if (!in && s2 <= a.Thi) {
-                if (ndef == 0) {
-                    def0 = p;
-                    ud0 = u;
-                } else {
-                    def1 = p;
-                    ud1 = u;
-                }
-                ++ndef;
-            }
+            nband += (!in && s2 <= a.Thi) ? 1 : 0;
             const float x = R.mrho0 * sinu;
             const float y = fmaf(R.D, h, R.C);
             const float xx = x * x;
@@ -169,8 +159,9 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             nm += nrun;
         }
     }
-    if (ndef > 2) {
-        // cannot happen for HEALPix spacings; redo the guard-band pairs one by one
+    if (nband > 0) {
+        // rare: the guard-band pairs, found again and decided in float64 (u and
+        // s^2 are recomputed exactly as in the loop)
         int kk = kk0;
         float kf = (float)kl;
         for (int k = kl; k <= kh; ++k) {
@@ -184,10 +175,7 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             if (s2 >= a.Tlo && s2 <= a.Thi && exact_member(a, pix, p))
                 pixel_pair<KIND, MODE>(a, R, qtab, u, p, pe, pb, pv, pw, nn, nm);
         }
-        return;
     }
-    if (ndef >= 1 && exact_member(a, pix, def0)) pixel_pair<KIND, MODE>(a, R, qtab, ud0, def0, pe, pb, pv, pw, nn, nm);
-    if (ndef >= 2 && exact_member(a, pix, def1)) pixel_pair<KIND, MODE>(a, R, qtab, ud1, def1, pe, pb, pv, pw, nn, nm);
 }
 
 // galaxies in the bin pixels [lo, lo + len) of a ring (indices mod nr)
