@@ -308,7 +308,8 @@ def run_native_pixel(args, world, rank):
     flops = FLOPS_PER_PAIR[wl.filter]
     roof, per_kernel = kernel_roofline(
         ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, flops, "k_pixel_toeplitz"),
-              "pixel_general": (pairs_gen, flops, "k_pixel_general")},
+              "pixel_general": (pairs_gen, flops, "k_pixel_general"),
+              "pixel_band": (0, flops, "k_pixel_band")},
         args.workload, FP32_PEAK_TFLOPS, PEAK_SOURCE)
     ctx.timing(False)
     npix_bin = 12 * wl.nside ** 2

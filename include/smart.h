@@ -283,7 +283,8 @@ typedef enum {
     SMART_KT_BIN_PIXEL_SUMS = 8,   /* smart_bin_galaxies: per-pixel sums */
     SMART_KT_BARY_BUILD = 9,       /* smart_map_barycentre: barycentre records (once per catalogue) */
     SMART_KT_BARY_MAP = 10,        /* smart_map_barycentre: main kernel */
-    SMART_KT_COUNT = 11
+    SMART_KT_PIXEL_BAND = 11,      /* pixel mode, float64 decisions of the general kernel's guard-band pairs */
+    SMART_KT_COUNT = 12
 } smart_kernel_id;
 
 /*

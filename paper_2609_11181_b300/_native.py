@@ -16,7 +16,8 @@ STATUS = {0: "SMART_OK", 1: "SMART_E_ARG", 2: "SMART_E_NOMEM", 3: "SMART_E_CUDA"
           5: "SMART_E_TIMEOUT", 6: "SMART_E_OVERFLOW", 7: "SMART_E_INTERNAL"}
 
 KERNELS = {"pixel_toeplitz": 0, "pixel_general": 1, "galaxy": 2, "galaxy_band": 3, "galaxy_finalise": 4,
-           "bin_keys": 5, "bin_sort": 6, "bin_records": 7, "bin_pixel_sums": 8, "bary_build": 9, "bary_map": 10}
+           "bin_keys": 5, "bin_sort": 6, "bin_records": 7, "bin_pixel_sums": 8, "bary_build": 9, "bary_map": 10,
+           "pixel_band": 11}
 
 MLP_FEATURES = 4
 MLP_NPARAMS = 4545

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_batched(const MapArgs *__restri
 // staged in shared memory; entries of another map read theirs from global.
 template <int KIND>
 __global__ void __launch_bounds__(128, 5) k_pixel_batched_general(const MapArgs *__restrict__ maps,
-                                                                   const int2 *__restrict__ list, int64_t n) {
+                                                                   const int2 *__restrict__ list, int64_t n,
+                                                                   const GenBand gb) {
     __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x;
     const int m0 = list[i0].x;
@@ -65,7 +66,22 @@ __global__ void __launch_bounds__(128, 5) k_pixel_batched_general(const MapArgs 
     if (i >= n) return;
     const int2 e = list[i];
     const MapArgs &a = maps[e.x];
-    general_target<KIND>(a, e.y, e.x == m0 ? qtab : a.f.qtab);
+    general_target<KIND>(a, e.y, i, e.x == m0 ? qtab : a.f.qtab, gb);
+}
+
+// the general targets with guard-band pairs, one thread per slot
+template <int KIND>
+__global__ void k_pixel_batched_band(const MapArgs *__restrict__ maps, const int2 *__restrict__ list,
+                                     const GenBand gb) {
+    const unsigned long long n = min(*gb.counts, (unsigned long long)gb.cap_slots);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const int2 e = list[gb.idx[i]];
+        const MapArgs &a = maps[e.x];
+        const double *raw = gb.raw + 4 * i;
+        band_finish<KIND>(a, e.y, a.f.qtab, gb.mask[i], raw[0], raw[1], raw[2], raw[3], gb.cnt[2 * i],
+                          gb.cnt[2 * i + 1]);
+    }
 }
 
 __global__ void k_tiles_wanted(const MapArgs a, unsigned char *__restrict__ want) {
@@ -86,6 +102,9 @@ struct smart_batch {
     int64_t n_items = 0;
     int2 *d_gen = nullptr;           // (map, target) of every general target
     int64_t n_gen = 0;
+    void *d_band = nullptr;          // slots of general targets with guard-band pairs
+    unsigned long long *d_band_count = nullptr;
+    GenBand gb{};
     int *d_work = nullptr;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;     // the general kernel runs here, beside the persistent kernel
@@ -134,10 +153,15 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
     if (b->n_gen > 0) {
         cudaStream_t gs = fork ? b->side : b->stream;
         const unsigned grid = (unsigned)((b->n_gen + 127) / 128);
-        if (b->kind == SMART_FILTER_POLY)
-            k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen);
-        else
-            k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen);
+        if (cudaMemsetAsync(b->d_band_count, 0, sizeof(unsigned long long), gs) != cudaSuccess)
+            return bfail(b, SMART_E_CUDA, "slot counter reset failed");
+        if (b->kind == SMART_FILTER_POLY) {
+            k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen, b->gb);
+            k_pixel_batched_band<SMART_FILTER_POLY><<<sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
+        } else {
+            k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen, b->gb);
+            k_pixel_batched_band<SMART_FILTER_SCHIRMER><<<sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
+        }
     }
     if (b->n_items > 0) {
         const unsigned grid = (unsigned)std::min<int64_t>(b->n_items, (int64_t)sms * ctas_per_sm);
@@ -172,6 +196,8 @@ extern "C" void smart_batch_destroy(smart_batch *b) {
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_gen) cudaFree(b->d_gen);
     if (b->d_work) cudaFree(b->d_work);
+    if (b->d_band) cudaFree(b->d_band);
+    if (b->d_band_count) cudaFree(b->d_band_count);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     if (b->side) {
         cudaStreamSynchronize(b->side);
@@ -286,11 +312,14 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     if (cudaMalloc(&b->d_maps, sizeof(MapArgs) * n_maps) != cudaSuccess ||
         cudaMalloc(&b->d_items, sizeof(BatchItem) * 2 * nb) != cudaSuccess ||
         cudaMalloc(&b->d_gen, sizeof(int2) * std::max<size_t>(1, gen.size())) != cudaSuccess ||
-        cudaMalloc(&b->d_work, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&b->d_work, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_band, (size_t)(GEN_BAND_SLOT_BYTES * gen_band_slots(b->n_gen))) != cudaSuccess ||
+        cudaMalloc(&b->d_band_count, sizeof(unsigned long long)) != cudaSuccess) {
         bfail(b, SMART_E_NOMEM, "cudaMalloc(batch tables) failed");
         smart_batch_destroy(b);
         return SMART_E_NOMEM;
     }
+    b->gb = gen_band_layout(b->d_band, gen_band_slots(b->n_gen), b->d_band_count);
     cudaMemcpyAsync(b->d_maps, b->args.data(), sizeof(MapArgs) * n_maps, cudaMemcpyHostToDevice, b->stream);
     if (!gen.empty())
         cudaMemcpyAsync(b->d_gen, gen.data(), sizeof(int2) * gen.size(), cudaMemcpyHostToDevice, b->stream);

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT, 4) k_pixel_toeplitz(const MapArgs a) {
 // threads hold consecutive targets, so bin pixels are read coalesced.
 // ------------------------------------------------------------------------
 template <int KIND>
-__global__ void __launch_bounds__(128, 5) k_pixel_general(const MapArgs a) {
+__global__ void __launch_bounds__(128, 5) k_pixel_general(const __grid_constant__ MapArgs a, const GenBand gb) {
     __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
     if (KIND != SMART_FILTER_POLY) {
         for (int i = threadIdx.x; i < QTAB_BINS; i += blockDim.x) qtab[i] = a.f.qtab[i];
@@ -174,7 +174,25 @@ __global__ void __launch_bounds__(128, 5) k_pixel_general(const MapArgs a) {
     }
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= a.n_gen) return;
-    general_target<KIND>(a, a.gen_list[idx], qtab);
+    general_target<KIND>(a, a.gen_list[idx], idx, qtab, gb);
+}
+
+// the general kernel's targets with guard-band pairs, one thread per slot:
+// float64 decisions of those pairs, then normalisation
+template <int KIND>
+__global__ void k_pixel_band(const MapArgs a, const GenBand gb) {
+    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
+    if (KIND != SMART_FILTER_POLY) {
+        for (int i = threadIdx.x; i < QTAB_BINS; i += blockDim.x) qtab[i] = a.f.qtab[i];
+        __syncthreads();
+    }
+    const unsigned long long n = min(*gb.counts, (unsigned long long)gb.cap_slots);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const double *raw = gb.raw + 4 * i;
+        band_finish<KIND>(a, a.gen_list[gb.idx[i]], qtab, gb.mask[i], raw[0], raw[1], raw[2], raw[3], gb.cnt[2 * i],
+                          gb.cnt[2 * i + 1]);
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -467,6 +485,18 @@ smart_status prepare_pixel(smart_ctx *c, const smart_maps *out, MapArgs &a) {
     return SMART_OK;
 }
 
+// slots of the general kernel's targets with guard-band pairs (a target
+// without a free slot is finished in place); counter reset on the stream
+smart_status general_band_buffers(smart_ctx *c, int64_t n_gen, GenBand &gb) {
+    const int64_t slots = gen_band_slots(n_gen);
+    smart_status st = ensure_alloc(c, &c->gen_band, c->cap_gen_band, slots, GEN_BAND_SLOT_BYTES, "guard-band slots");
+    if (st != SMART_OK) return st;
+    st = ensure_alloc(c, (void **)&c->d_gen_count, c->cap_gen_count, 1, sizeof(unsigned long long), "slot counter");
+    if (st != SMART_OK) return st;
+    gb = gen_band_layout(c->gen_band, slots, c->d_gen_count);
+    return check_cuda(c, cudaMemsetAsync(c->d_gen_count, 0, sizeof(unsigned long long), c->stream), "slot counter");
+}
+
 smart_status launch_count_prefix(smart_ctx *c) {
     if (c->binned_from_catalog && c->have_catalog) return SMART_OK;
     const int64_t npix = npix_of(c->nside_bin);
@@ -495,11 +525,22 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
         if (st != SMART_OK) return st;
     }
     if (a.n_gen > 0) {
-        const unsigned grid = (unsigned)((a.n_gen + 127) / 128);
-        KernelTimer timer(c, SMART_KT_PIXEL_GENERAL);
-        if (c->filter_kind == SMART_FILTER_POLY) k_pixel_general<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a);
-        else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a);
-        st = check_cuda(c, cudaGetLastError(), "k_pixel_general launch");
+        GenBand gb{};
+        if ((st = general_band_buffers(c, a.n_gen, gb)) != SMART_OK) return st;
+        const bool poly = c->filter_kind == SMART_FILTER_POLY;
+        {
+            const unsigned grid = (unsigned)((a.n_gen + 127) / 128);
+            KernelTimer timer(c, SMART_KT_PIXEL_GENERAL);
+            if (poly) k_pixel_general<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a, gb);
+            else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a, gb);
+        }
+        {
+            KernelTimer timer(c, SMART_KT_PIXEL_BAND);
+            const unsigned grid = (unsigned)c->num_sms;
+            if (poly) k_pixel_band<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a, gb);
+            else k_pixel_band<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a, gb);
+        }
+        st = check_cuda(c, cudaGetLastError(), "general kernel launches");
     }
     if (st == SMART_OK && averaged) st = averaged_rescale(c, out);
     return st;

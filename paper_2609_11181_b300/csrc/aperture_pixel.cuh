@@ -87,16 +87,12 @@ __device__ __forceinline__ void pixel_pair(const MapArgs &a, const RingPair &R, 
     nm += 1;
 }
 
-// pixel-mode general pair loop for one target and one ring pair; MODE picks
-// the sine series by the largest |u| of the ring pair (0: <= 0.05 rad,
-// 1: <= 0.45 rad, 2: |u| <= pi).  Pairs inside the float32 guard band are
-// only counted in the loop, which keeps its body free of branches; when
-// there are any (rarely), the window is scanned again and they are decided
-// in float64 after the loop.
+// the guard-band pairs of one target and one ring pair, decided in float64
+// (window, u and s^2 exactly as in general_segment)
 template <int KIND, int MODE>
-__device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
-                                                const LatticeDiv &ld, int64_t pix, const float4 *qtab, float &pe,
-                                                float &pb, float &pv, float &pw, int &nn, int &nm) {
+__device__ __forceinline__ void band_pairs(const MapArgs &a, const RingPair &R, const TargetRing &tr,
+                                           const LatticeDiv &ld, int64_t pix, const float4 *qtab, float &pe,
+                                           float &pb, float &pv, float &pw, int &nn, int &nm) {
     const int q = R.nr >> 2;
     int Xi;
     float Xf;
@@ -104,79 +100,152 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
     const float fr = ((R.flags & RP_SHIFTED) ? 0.5f : 0.0f) - Xf;
     int kl, kh;
     window(R, fr, kl, kh);
-    // 0 <= Xi < nr and kl > -nr: one correction brings the start into [0, nr)
-    int kk0 = Xi + kl;
-    kk0 += kk0 < 0 ? R.nr : (kk0 >= R.nr ? -R.nr : 0);
+    int kk = Xi + kl;
+    kk += kk < 0 ? R.nr : (kk >= R.nr ? -R.nr : 0);
     const float u0 = fr * R.dphi;
-    int nband = 0;          // pairs inside the float32 guard band
-    // the window's pixels are [kk0, nr) then [0, rest) when it wraps
-    const int len = kh - kl + 1;
-    const int n1 = min(len, R.nr - kk0);
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-        const int cnt = part == 0 ? n1 : len - n1;
-        if (cnt <= 0) continue;
-        const int pbeg = part == 0 ? R.start + kk0 : R.start;
-        const int plast = pbeg + cnt - 1;
-        float kf = (float)(part == 0 ? kl : kl + n1);
-        // the bin pixel's data is loaded one iteration ahead (the load of the
-        // last pixel is repeated, never past the run)
-        float4 gn = __ldg(a.PX + pbeg);
-        // the strict members of a run are contiguous (s^2 grows with |u|): their
-        // number and the last one give the galaxy count from the count prefix
-        int nrun = 0, last = -1;
-        // branch-free body (non-members add zeros), so that consecutive pairs
-        // can interleave; guard-band pairs take the rare branch
-#pragma unroll 2
-        for (int i = 0; i < cnt; ++i) {
-            const int p = pbeg + i;
-            const float4 g = gn;
-            gn = __ldg(a.PX + min(p + 1, plast));
-            const float u = fmaf(kf, R.dphi, u0);
-            kf += 1.0f;
-            float sinu, h;
-            sin_hav<MODE>(u, sinu, h);
-            const float s2 = fmaf(R.B, h, R.A);
-            const bool in = s2 < a.Tlo;
-            nband += (!in && s2 <= a.Thi) ? 1 : 0;
-            const float x = R.mrho0 * sinu;
-            const float y = fmaf(R.D, h, R.C);
-            const float xx = x * x;
-            const float sd2 = fmaf(y, y, xx);
-            const float cc = fmaf(y, y, -xx);
-            const float ss = -2.0f * x * y;
-            const float Q = filter_Q<KIND>(a.f, qtab, s2);
-            const float w = (in && sd2 > 1e-30f) ? __fdividef(Q, sd2) : 0.f;
-            pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
-            pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
-            pv = fmaf(in ? Q * Q : 0.f, g.z, pv);
-            pw += in ? g.w : 0.f;
-            nrun += in ? 1 : 0;
-            last = in ? i : last;
-        }
-        if (nrun > 0) {
-            nn += __ldg(a.NPRE + pbeg + last + 1) - __ldg(a.NPRE + pbeg + last + 1 - nrun);
-            nm += nrun;
-        }
-    }
-    if (nband > 0) {
-        // rare: the guard-band pairs, found again and decided in float64 (u and
-        // s^2 are recomputed exactly as in the loop)
-        int kk = kk0;
-        float kf = (float)kl;
-        for (int k = kl; k <= kh; ++k) {
-            const float u = fmaf(kf, R.dphi, u0);
-            kf += 1.0f;
-            float sinu, h;
-            sin_hav<MODE>(u, sinu, h);
-            const float s2 = fmaf(R.B, h, R.A);
-            const int p = R.start + kk;
-            kk = (kk + 1 == R.nr) ? 0 : kk + 1;
-            if (s2 >= a.Tlo && s2 <= a.Thi && exact_member(a, pix, p))
-                pixel_pair<KIND, MODE>(a, R, qtab, u, p, pe, pb, pv, pw, nn, nm);
-        }
+    float kf = (float)kl;
+    for (int k = kl; k <= kh; ++k) {
+        const float u = fmaf(kf, R.dphi, u0);
+        kf += 1.0f;
+        float sinu, h;
+        sin_hav<MODE>(u, sinu, h);
+        const float s2 = fmaf(R.B, h, R.A);
+        const int p = R.start + kk;
+        kk = (kk + 1 == R.nr) ? 0 : kk + 1;
+        if (s2 >= a.Tlo && s2 <= a.Thi && exact_member(a, pix, p))
+            pixel_pair<KIND, MODE>(a, R, qtab, u, p, pe, pb, pv, pw, nn, nm);
     }
 }
+
+// position in the bin ring of lattice offset k (0 <= Xi < nr, -nr < k < nr)
+__device__ __forceinline__ int wrap_start(const RingPair &R, int Xi, int k) {
+    int kk = Xi + k;
+    kk += kk < 0 ? R.nr : (kk >= R.nr ? -R.nr : 0);
+    return kk;
+}
+
+// pixel-mode general pair loop for one target and one ring pair; MODE picks
+// the sine series by the largest |u| of the ring pair (0: <= 0.05 rad,
+// 1: <= 0.45 rad, 2: |u| <= pi).  Offsets within hw_in are members for
+// certain: their loop has no test at all, and their galaxy count comes from
+// the count prefix.  The few offsets between hw_in and the window's edges
+// are tested; those inside the float32 guard band are only counted
+// (nband_out): they are decided in float64 once the target's other pairs
+// are summed.
+template <int KIND, int MODE>
+__device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
+                                                const LatticeDiv &ld, const float4 *qtab, float &pe, float &pb,
+                                                float &pv, float &pw, int &nn, int &nm, int &nband_out) {
+    const int q = R.nr >> 2;
+    int Xi;
+    float Xf;
+    lattice_position(tr, ld, q, Xi, Xf);
+    const float fr = ((R.flags & RP_SHIFTED) ? 0.5f : 0.0f) - Xf;
+    int kl, kh;
+    window(R, fr, kl, kh);
+    int il = max(kl, (int)ceilf(-fr - R.hw_in)), ih = min(kh, (int)floorf(-fr + R.hw_in));
+    if (il > ih) {                        // no certain member: the whole window is tested
+        il = kh + 1;
+        ih = kh;
+    }
+    const float u0 = fr * R.dphi;
+    // certain members: bin pixels [kk0, nr) then [0, ...) when they wrap
+    const int len = ih - il + 1;
+    if (len > 0) {
+        const int kk0 = wrap_start(R, Xi, il);
+        const int n1 = min(len, R.nr - kk0);
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {
+            const int cnt = part == 0 ? n1 : len - n1;
+            if (cnt <= 0) continue;
+            const int pbeg = part == 0 ? R.start + kk0 : R.start;
+            const int plast = pbeg + cnt - 1;
+            float kf = (float)(part == 0 ? il : il + n1);
+            // the bin pixel's data is loaded one iteration ahead (the load of
+            // the last pixel is repeated, never past the run)
+            float4 gn = __ldg(a.PX + pbeg);
+#pragma unroll 2
+            for (int i = 0; i < cnt; ++i) {
+                const float4 g = gn;
+                gn = __ldg(a.PX + min(pbeg + i + 1, plast));
+                const float u = fmaf(kf, R.dphi, u0);
+                kf += 1.0f;
+                float sinu, h;
+                sin_hav<MODE>(u, sinu, h);
+                const float s2 = fmaf(R.B, h, R.A);
+                const float x = R.mrho0 * sinu;
+                const float y = fmaf(R.D, h, R.C);
+                const float xx = x * x;
+                const float sd2 = fmaf(y, y, xx);
+                const float cc = fmaf(y, y, -xx);
+                const float ss = -2.0f * x * y;
+                const float Q = filter_Q<KIND>(a.f, qtab, s2);
+                // sd2 = 0 only at the target's own centre, where cc = ss = 0
+                // exactly; elsewhere sd2 is at least a squared bin spacing, far
+                // above the offset, which only keeps w finite there
+                const float w = __fdividef(Q, sd2 + 1e-30f);
+                pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
+                pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
+                pv = fmaf(Q * Q, g.z, pv);
+                pw += g.w;
+            }
+            nn += __ldg(a.NPRE + plast + 1) - __ldg(a.NPRE + pbeg);
+            nm += cnt;
+        }
+    }
+    // the offsets between the certain members and the window's edges
+    int nband = 0;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int ka = side == 0 ? kl : ih + 1, kb = side == 0 ? il - 1 : kh;
+        for (int k = ka; k <= kb; ++k) {
+            const float u = fmaf((float)k, R.dphi, u0);
+            float sinu, h;
+            sin_hav<MODE>(u, sinu, h);
+            const float s2 = fmaf(R.B, h, R.A);
+            if (s2 < a.Tlo) pixel_pair<KIND, MODE>(a, R, qtab, u, R.start + wrap_start(R, Xi, k), pe, pb, pv, pw, nn, nm);
+            else nband += s2 <= a.Thi ? 1 : 0;
+        }
+    }
+    nband_out = nband;
+}
+
+// Targets of the general kernel with guard-band pairs.  Such a target takes
+// a slot for its raw sums and a mask of the ring-pair entries that hold
+// those pairs (bit e for entry e < 63, bit 63 for every entry from 63 on);
+// one thread per slot then decides them in float64 and normalises the
+// target.  A target that finds no free slot does the same in place, with
+// the same code, so the result never depends on which of the two ran.
+struct GenBand {
+    double *raw;                   // 4 per slot: SE, SB, SV, SW
+    int32_t *cnt;                  // 2 per slot: galaxies, member pixels
+    int64_t *idx;                  // the target's position in its general list
+    unsigned long long *mask;      // ring-pair entries with guard-band pairs
+    unsigned long long *counts;    // [0]: slots claimed
+    int64_t cap_slots;
+};
+
+constexpr int64_t GEN_BAND_SLOT_BYTES = 4 * sizeof(double) + sizeof(int64_t) + sizeof(unsigned long long) +
+                                        2 * sizeof(int32_t);
+
+// the slot arrays in one allocation of slots * GEN_BAND_SLOT_BYTES bytes
+inline GenBand gen_band_layout(void *buf, int64_t slots, unsigned long long *counts) {
+    GenBand gb;
+    char *p = (char *)buf;
+    gb.raw = (double *)p;
+    p += slots * 4 * sizeof(double);
+    gb.idx = (int64_t *)p;
+    p += slots * sizeof(int64_t);
+    gb.mask = (unsigned long long *)p;
+    p += slots * sizeof(unsigned long long);
+    gb.cnt = (int32_t *)p;
+    gb.counts = counts;
+    gb.cap_slots = slots;
+    return gb;
+}
+
+// slots for n general targets (a small share of them has guard-band pairs)
+inline int64_t gen_band_slots(int64_t n) { return (1 << 16) + n / 8; }
 
 // galaxies in the bin pixels [lo, lo + len) of a ring (indices mod nr)
 __device__ __forceinline__ int ring_range_count(const int32_t *pre, int start, int nr, int lo, int len) {
@@ -217,21 +286,39 @@ static_assert(PREN % 4 == 0, "prefix planes");
 
 __device__ __forceinline__ int ppos(int m) { return (m & 3) * PREQ + (m >> 2); }
 
+// what a tile needs of one of its ring pairs; the tile's first TPN ring
+// pairs are read into shared memory once, at the start of the tile
 struct ToeStage {
-    int start, nr, k0, L, off;
+    int start, nr, k0, L, off, da, tot, namb;
 };
+constexpr int TPN = 64;
 
-// issue the copies of ring pair e of a tile into buffer b
-__device__ __forceinline__ ToeStage toe_stage(const MapArgs &a, int64_t row0, int e, int jbase, int nslots,
-                                              float4 (*seg)[SEGN], float4 (*geo)[NCAND], int (*pre)[PREN], int b,
-                                              int tid) {
+__device__ __forceinline__ ToeStage toe_param(const MapArgs &a, int64_t row0, int e) {
     ToeStage t;
     t.start = __ldg(&a.table[row0 + e].start);
     t.nr = __ldg(&a.table[row0 + e].nr);
     const ToeInfo ti = a.toe[row0 + e];
     t.L = ti.L;
     t.off = ti.off;
-    t.k0 = jbase + ti.dlo + ti.da;
+    t.da = ti.da;
+    t.k0 = ti.dlo + ti.da;                 // relative to the tile's first slot
+    t.namb = ti.namb;
+    t.tot = __ldg(a.NPRE + t.start + t.nr) - __ldg(a.NPRE + t.start);   // galaxies on the bin ring
+    return t;
+}
+
+__device__ __forceinline__ ToeStage tile_param(const MapArgs &a, const ToeStage *par, int64_t row0, int e,
+                                               int jbase) {
+    ToeStage t = e < TPN ? par[e] : toe_param(a, row0, e);
+    t.k0 += jbase;
+    return t;
+}
+
+// issue the copies of ring pair e of a tile into buffer b
+__device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par, int64_t row0, int e, int jbase,
+                                          int nslots, float4 (*seg)[SEGN], float4 (*geo)[NCAND], int (*pre)[PREN],
+                                          int b, int tid) {
+    const ToeStage t = tile_param(a, par, row0, e, jbase);
     if (t.L > 0) {
         const int nseg = min(SEGN, nslots + t.L + 3);
         const int nseg32 = (nseg + 31) & ~31;
@@ -243,7 +330,7 @@ __device__ __forceinline__ ToeStage toe_stage(const MapArgs &a, int64_t row0, in
             kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
             cp_async16(&seg[b][q], a.PX + t.start + kk);
         }
-        for (int c = tid; c < t.L; c += NT) cp_async16(&geo[b][c], a.toe_geo + ti.off + ti.da + c);
+        for (int c = tid; c < t.L; c += NT) cp_async16(&geo[b][c], a.toe_geo + t.off + t.da + c);
         const int npre = min(PREN, nslots + t.L + 1);
         for (int m = tid; m < npre; m += NT) {
             int kk = t.k0 + m;
@@ -252,7 +339,6 @@ __device__ __forceinline__ ToeStage toe_stage(const MapArgs &a, int64_t row0, in
         }
     }
     cp_async_commit();
-    return t;
 }
 
 struct ToeShared {
@@ -260,6 +346,7 @@ struct ToeShared {
     float4 geo[2][NCAND];
     int pre[2][PREN];
     int slot_t[TS];
+    ToeStage par[TPN];
 };
 
 // one tile of a Toeplitz output ring, summed by the whole CTA (NT threads);
@@ -279,11 +366,12 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
     const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
     const int nent = a.counts[tr0.i0 - 1];
     for (int s = tid; s < TS; s += NT) slot_t[s] = -1;
+    for (int e = tid; e < min(nent, TPN); e += NT) S.par[e] = toe_param(a, row0, e);
     __syncthreads();
     for (int64_t t = tb + tid; t < te; t += NT) slot_t[(int)(a.targets[t] - ring_start0) - jbase] = (int)(t - tb);
+    __syncthreads();      // slot map and ring-pair parameters written
 
-    ToeStage cur = toe_stage(a, row0, 0, jbase, nslots, seg, geo, pre, 0, tid);
-    __syncthreads();      // slot map written
+    toe_stage(a, S.par, row0, 0, jbase, nslots, seg, geo, pre, 0, tid);
 
     const int s0 = RB * tid;
     int tix[RB];
@@ -305,8 +393,8 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
         const int b = e & 1;
         cp_async_wait_all();
         __syncthreads();       // ring pair e staged; everyone is done with buffer b ^ 1
-        ToeStage nxt;
-        if (e + 1 < nent) nxt = toe_stage(a, row0, e + 1, jbase, nslots, seg, geo, pre, b ^ 1, tid);
+        if (e + 1 < nent) toe_stage(a, S.par, row0, e + 1, jbase, nslots, seg, geo, pre, b ^ 1, tid);
+        const ToeStage cur = tile_param(a, S.par, row0, e, jbase);
         const int L = cur.L;
         if (L > 0 && any) {
             float pe[RB], pb[RB], pv[RB], pw[RB];
@@ -365,7 +453,7 @@ pw[r] += P.w;
 #undef SMART_ACC
             // galaxies in [k0 + s, k0 + s + L) from the staged prefix, with the
             // ring total added for every pass over the ring's end
-            const int ring_tot = __ldg(a.NPRE + cur.start + cur.nr) - __ldg(a.NPRE + cur.start);
+            const int ring_tot = cur.tot;
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
                 if (tix[r] < 0) continue;
@@ -380,7 +468,7 @@ pw[r] += P.w;
             }
         }
         // ---- guard-band offsets: decided per target in float64
-        if (any && cur.off >= 0) {
+        if (any && cur.namb > 0) {
             const ToeInfo ti = a.toe[row0 + e];
             for (int ia = 0; ia < ti.namb; ++ia) {
                 const int c = ia == 0 ? ti.amb0 : (ia == 1 ? ti.amb1 : ti.amb2);
@@ -403,7 +491,6 @@ pw[r] += P.w;
                 }
             }
         }
-        cur = nxt;
     }
     cp_async_wait_all();
 #pragma unroll
@@ -419,9 +506,56 @@ __device__ __forceinline__ bool toeplitz_tile_wanted(const MapArgs &a, int64_t t
     return a.toe_ring[tr0.i0 - 1] != 0;
 }
 
-// one target of a general output ring (one thread)
+// guard-band pairs of the ring-pair entries in mask, then the summed
+// normalisation (Sect. 2.4) of the target from its raw sums
 template <int KIND>
-__device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, const float4 *qtab) {
+__device__ __forceinline__ void band_finish(const MapArgs &a, int64_t t, const float4 *qtab, unsigned long long mask,
+                                            double se, double sb, double sv, double sw, int NN, int NM) {
+    const int64_t pix = a.targets[t];
+    const TargetRing tr = target_ring(a.N0, pix);
+    const LatticeDiv ld = lattice_div(tr);
+    const int64_t row0 = (int64_t)(tr.i0 - 1) * a.kmax;
+    const int nent = a.counts[tr.i0 - 1];
+    float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
+    for (int e = 0; e < nent; ++e) {
+        if (!((mask >> min(e, 63)) & 1ull)) continue;
+        const RingPair R = a.table[row0 + e];
+        const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
+        if (mode == 0) band_pairs<KIND, 0>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, NN, NM);
+        else if (mode == 1) band_pairs<KIND, 1>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, NN, NM);
+        else band_pairs<KIND, 2>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, NN, NM);
+    }
+    const double SW = sw + (double)pw;
+    float me = 0.f, mb = 0.f, vv = 0.f;
+    if (SW > 0.0) {
+        const float r = (float)a.area / (float)SW;       // 1 / nbar
+        me = (float)(se + (double)pe) * r;
+        mb = (float)(sb + (double)pb) * r;
+        vv = 0.5f * (float)(sv + (double)pv) * r * r;
+    }
+    if (a.sum_w) a.sum_w[t] = SW;
+    if (a.map_e) a.map_e[t] = me;
+    if (a.map_b) a.map_b[t] = mb;
+    if (a.var) a.var[t] = vv;
+    if (a.count) a.count[t] = NN;
+    if (a.members) a.members[t] = NM;
+}
+
+// band_finish out of line, for the rare target that finds no free slot (a
+// call keeps the general loop's registers free of it); a points to a
+// __grid_constant__ kernel parameter or to global memory
+template <int KIND>
+__device__ __noinline__ void band_finish_call(const MapArgs *a, int64_t t, const float4 *qtab,
+                                              unsigned long long mask, double se, double sb, double sv, double sw,
+                                              int NN, int NM) {
+    band_finish<KIND>(*a, t, qtab, mask, se, sb, sv, sw, NN, NM);
+}
+
+// one target of a general output ring (one thread); gidx is its position in
+// the general list.  Guard-band pairs are left to band_finish.
+template <int KIND>
+__device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, int64_t gidx, const float4 *qtab,
+                                               const GenBand &gb) {
     const int64_t pix = a.targets[t];
     const TargetRing tr = target_ring(a.N0, pix);
     const LatticeDiv ld = lattice_div(tr);
@@ -429,14 +563,16 @@ __device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, cons
     const int nent = a.counts[tr.i0 - 1];
     float SE = 0.f, cSE = 0.f, SB = 0.f, cSB = 0.f, SV = 0.f, SW = 0.f, cSW = 0.f;
     int NN = 0, NM = 0;
+    unsigned long long mask = 0;
     for (int e = 0; e < nent; ++e) {
         const RingPair R = a.table[row0 + e];
         const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
         float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
-        int nn = 0, nm = 0;
-        if (mode == 0) general_segment<KIND, 0>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, nn, nm);
-        else if (mode == 1) general_segment<KIND, 1>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, nn, nm);
-        else general_segment<KIND, 2>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, nn, nm);
+        int nn = 0, nm = 0, nb = 0;
+        if (mode == 0) general_segment<KIND, 0>(a, R, tr, ld, qtab, pe, pb, pv, pw, nn, nm, nb);
+        else if (mode == 1) general_segment<KIND, 1>(a, R, tr, ld, qtab, pe, pb, pv, pw, nn, nm, nb);
+        else general_segment<KIND, 2>(a, R, tr, ld, qtab, pe, pb, pv, pw, nn, nm, nb);
+        mask |= nb > 0 ? 1ull << min(e, 63) : 0ull;
         kahan_add(SE, cSE, pe);
         kahan_add(SB, cSB, pb);
         SV += pv;
@@ -444,7 +580,25 @@ __device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, cons
         NN += nn;
         NM += nm;
     }
-    finalise(a, t, SE, cSE, SB, cSB, SV, 0.f, SW, cSW, NN, NM);
+    if (!mask) {
+        finalise(a, t, SE, cSE, SB, cSB, SV, 0.f, SW, cSW, NN, NM);
+        return;
+    }
+    const double se = (double)SE - (double)cSE, sb = (double)SB - (double)cSB, sw = (double)SW - (double)cSW;
+    const unsigned long long slot = atomicAdd(gb.counts, 1ull);
+    if (slot < (unsigned long long)gb.cap_slots) {
+        double *raw = gb.raw + 4 * slot;
+        raw[0] = se;
+        raw[1] = sb;
+        raw[2] = (double)SV;
+        raw[3] = sw;
+        gb.cnt[2 * slot] = NN;
+        gb.cnt[2 * slot + 1] = NM;
+        gb.idx[slot] = gidx;
+        gb.mask[slot] = mask;
+    } else {
+        band_finish_call<KIND>(&a, t, qtab, mask, se, sb, (double)SV, sw, NN, NM);
+    }
 }
 
 }  // namespace smart

@@ -90,7 +90,7 @@ extern "C" void smart_destroy(smart_ctx *c) {
                     c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
                     c->toe_ring, c->gen_list, c->gal_tiles, c->raw, c->band, c->d_band_count,
                     c->d_status, c->d_fp64_count, c->bary_off, c->bary_geo, c->bary_sh, c->bary_keys,
-                    c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m, c->avg_buf};
+                    c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m, c->avg_buf, c->gen_band, c->d_gen_count};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -118,7 +118,7 @@ extern "C" smart_status smart_sync(smart_ctx *c, double timeout_s) {
     if (status) {
         cudaMemset(c->d_status, 0, sizeof(int));
         if (status & SMART_STATUS_BAND_OVERFLOW)
-            return fail(c, SMART_E_OVERFLOW, "guard-band pair list overflowed: brute-force map incomplete");
+            return fail(c, SMART_E_OVERFLOW, "guard-band pair list overflowed: map incomplete");
         return fail(c, SMART_E_INTERNAL, "device status " + std::to_string(status));
     }
     return SMART_OK;

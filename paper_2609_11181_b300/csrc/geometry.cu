@@ -72,8 +72,14 @@ __global__ void k_ring_pairs(int64_t N0, int64_t N1, double theta_disc, double T
         const double B = 4.0 * g.rho * g0.rho;
         const double dphi = 2.0 * SMART_PI / (double)g.nr;
         int flags = g.shifted ? RP_SHIFTED : 0;
-        double hw;
+        double hw, hw_in = -1.0;
         const double sn2 = (Tdisc - A) / B;
+        // certain members: s^2 <= T_disc (1 - 1e-5) for every offset within
+        // hw_in, after the float32 rounding of the offsets (relative 1e-6 of
+        // the window and 1e-3 bin pixels)
+        const double sn2_in = (Tdisc * (1.0 - 1e-5) - A) / B;
+        if (B > 0.0 && sn2_in >= 1.0) hw_in = (double)g.nr;
+        else if (B > 0.0 && sn2_in > 0.0) hw_in = 2.0 * asin(sqrt(sn2_in)) / dphi * (1.0 - 1e-6) - 1e-3;
         if (!(B > 0.0) || sn2 >= 1.0) {
             flags |= RP_WHOLE | RP_WIDE;
             hw = 0.5 * g.nr;
@@ -109,7 +115,7 @@ __global__ void k_ring_pairs(int64_t N0, int64_t N1, double theta_disc, double T
         e.dlat = (float)dlat;
         e.rho0 = (float)g0.rho;
         e.z0 = (float)g0.z;
-        e.pad0 = 0.f;
+        e.hw_in = (float)hw_in;
         e.pad1 = 0.f;
         row[c++] = e;
     }

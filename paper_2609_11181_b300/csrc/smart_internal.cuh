@@ -257,7 +257,9 @@ struct RingPair {
     float mrho0;    // -rho0
     float dlat;     // latitude(i0) - latitude(i), rad (galaxy offsets are relative to it)
     float rho0, z0; // output ring constants (float32)
-    float pad0, pad1;
+    float hw_in;    // half window of certain members: |offset| <= hw_in gives
+                    // s^2 <= T_disc (1 - 1e-5) (negative: none)
+    float pad1;
 };
 static_assert(sizeof(RingPair) == 64, "RingPair layout");
 
@@ -368,6 +370,10 @@ struct smart_ctx {
     int64_t cap_bary_wr = 0;
     int32_t *raw_m = nullptr;                        // member records per target
     int64_t cap_raw_m = 0;
+    void *gen_band = nullptr;                        // general kernel: guard-band slots
+    int64_t cap_gen_band = 0;
+    unsigned long long *d_gen_count = nullptr;       // general kernel: slots claimed
+    int64_t cap_gen_count = 0;
 
     // diagnostics
     unsigned long long *d_fp64_count = nullptr;
