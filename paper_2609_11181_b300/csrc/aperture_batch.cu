@@ -157,10 +157,10 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
             return bfail(b, SMART_E_CUDA, "slot counter reset failed");
         if (b->kind == SMART_FILTER_POLY) {
             k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen, b->gb);
-            k_pixel_batched_band<SMART_FILTER_POLY><<<sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
+            k_pixel_batched_band<SMART_FILTER_POLY><<<4 * sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
         } else {
             k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen, b->gb);
-            k_pixel_batched_band<SMART_FILTER_SCHIRMER><<<sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
+            k_pixel_batched_band<SMART_FILTER_SCHIRMER><<<4 * sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
         }
     }
     if (b->n_items > 0) {

@@ -536,7 +536,7 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
         }
         {
             KernelTimer timer(c, SMART_KT_PIXEL_BAND);
-            const unsigned grid = (unsigned)c->num_sms;
+            const unsigned grid = (unsigned)c->num_sms * 4;   // four CTAs per SM (registers allow four)
             if (poly) k_pixel_band<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a, gb);
             else k_pixel_band<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a, gb);
         }
