@@ -31,7 +31,7 @@ struct BatchItem {
 
 // the Toeplitz tiles of every map, claimed longest first by resident CTAs
 template <int KIND>
-__global__ void __launch_bounds__(NT, 4) k_pixel_batched(const MapArgs *__restrict__ maps,
+__global__ void __launch_bounds__(NT, 8) k_pixel_batched(const MapArgs *__restrict__ maps,
                                                           const BatchItem *__restrict__ items, int64_t n_items,
                                                           int *__restrict__ work) {
     __shared__ __align__(16) ToeShared S;
@@ -113,7 +113,7 @@ struct smart_batch {
     cudaGraphExec_t exec = nullptr;
     bool own_stream = false;
     int kind = 0;
-    int ctas_per_sm = 4;
+    int ctas_per_sm = 8;
     int order = 0;            // 0: longest first, 1: natural
     double tuned_ms = 0.0;
     std::string err;
@@ -346,7 +346,7 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         double best = 1e30;
-        const int shapes[] = {2, 3, 4};
+        const int shapes[] = {4, 6, 8};
         for (int order = 0; order < 2 && st == SMART_OK; ++order) {
             for (int cps : shapes) {
                 st = batch_launch(b, cps, order);       // warm

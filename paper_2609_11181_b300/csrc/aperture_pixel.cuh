@@ -25,9 +25,9 @@
 namespace smart {
 
 
-constexpr int TS = 512;           // azimuth slots per tile (aligned blocks of a ring)
-constexpr int TS_LOG2 = 9;
-constexpr int NT = 128;           // threads per CTA
+constexpr int TS = 256;           // azimuth slots per tile (aligned blocks of a ring)
+constexpr int TS_LOG2 = 8;
+constexpr int NT = 64;            // threads per CTA
 constexpr int RB = 4;             // consecutive slots per thread
 constexpr int NCAND = 120;        // longest Toeplitz candidate run kept in shared memory
 constexpr int SEGN = TS + NCAND + 8;
