@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(NT, 8) k_pixel_batched(const MapArgs *__restri
 // The list runs map by map, so the filter table of the block's first map is
 // staged in shared memory; entries of another map read theirs from global.
 template <int KIND>
-__global__ void __launch_bounds__(128, 5) k_pixel_batched_general(const MapArgs *__restrict__ maps,
+__global__ void __launch_bounds__(128, 7) k_pixel_batched_general(const MapArgs *__restrict__ maps,
                                                                    const int2 *__restrict__ list, int64_t n,
                                                                    const GenBand gb) {
     __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];

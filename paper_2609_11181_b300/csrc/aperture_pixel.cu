@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT, 8) k_pixel_toeplitz(const MapArgs a) {
 // threads hold consecutive targets, so bin pixels are read coalesced.
 // ------------------------------------------------------------------------
 template <int KIND>
-__global__ void __launch_bounds__(128, 5) k_pixel_general(const __grid_constant__ MapArgs a, const GenBand gb) {
+__global__ void __launch_bounds__(128, 7) k_pixel_general(const __grid_constant__ MapArgs a, const GenBand gb) {
     __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
     if (KIND != SMART_FILTER_POLY) {
         for (int i = threadIdx.x; i < QTAB_BINS; i += blockDim.x) qtab[i] = a.f.qtab[i];
