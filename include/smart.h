@@ -312,6 +312,16 @@ smart_status smart_timing_read(smart_ctx *ctx, int kernel, int64_t *launches, do
  */
 smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_gen);
 
+/*
+ * Testing aid (no counterpart in the paper).  In the pixel map, a target of
+ * the general kernel with pairs inside the float32 guard band takes a slot
+ * whose float64 decisions a follow-up kernel makes; a target that finds no
+ * free slot makes them itself, with the same code.  n_slots > 0 caps the
+ * slots at n_slots so that tests can run that second path; 0 restores the
+ * default (65536 + n_general / 8).  SMART_E_ARG for n_slots < 0.  Host only.
+ */
+smart_status smart_set_band_slot_limit(smart_ctx *ctx, int64_t n_slots);
+
 /* ---- learned residual correction of the pixel-based map ------------ */
 
 /*

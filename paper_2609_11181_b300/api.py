@@ -217,6 +217,10 @@ class Context:
         self.sync(60)
         return idx.long()
 
+    def set_band_slot_limit(self, n_slots: int):
+        """Testing aid: cap the general kernel's guard-band slots (0: default)."""
+        self._check(self._lib.smart_set_band_slot_limit(self._h, int(n_slots)), "smart_set_band_slot_limit")
+
     # -- inspection
     def get_catalog(self, n: int):
         dev = torch.device("cuda", torch.cuda.current_device())

@@ -488,7 +488,7 @@ smart_status prepare_pixel(smart_ctx *c, const smart_maps *out, MapArgs &a) {
 // slots of the general kernel's targets with guard-band pairs (a target
 // without a free slot is finished in place); counter reset on the stream
 smart_status general_band_buffers(smart_ctx *c, int64_t n_gen, GenBand &gb) {
-    const int64_t slots = gen_band_slots(n_gen);
+    const int64_t slots = c->band_slot_limit > 0 ? c->band_slot_limit : gen_band_slots(n_gen);
     smart_status st = ensure_alloc(c, &c->gen_band, c->cap_gen_band, slots, GEN_BAND_SLOT_BYTES, "guard-band slots");
     if (st != SMART_OK) return st;
     st = ensure_alloc(c, (void **)&c->d_gen_count, c->cap_gen_count, 1, sizeof(unsigned long long), "slot counter");

@@ -284,6 +284,13 @@ extern "C" smart_status smart_timing_read(smart_ctx *c, int kernel, int64_t *lau
     return SMART_OK;
 }
 
+extern "C" smart_status smart_set_band_slot_limit(smart_ctx *c, int64_t n_slots) {
+    if (!c) return SMART_E_ARG;
+    if (n_slots < 0) return fail(c, SMART_E_ARG, "smart_set_band_slot_limit: negative limit");
+    c->band_slot_limit = n_slots;
+    return SMART_OK;
+}
+
 extern "C" smart_status smart_get_general_targets(smart_ctx *c, int32_t *idx, int64_t cap, int64_t *n_gen) {
     if (!c || !n_gen) return SMART_E_ARG;
     if (c->gen_version != c->targets_version)

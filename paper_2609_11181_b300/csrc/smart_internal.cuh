@@ -374,6 +374,7 @@ struct smart_ctx {
     int64_t cap_gen_band = 0;
     unsigned long long *d_gen_count = nullptr;       // general kernel: slots claimed
     int64_t cap_gen_count = 0;
+    int64_t band_slot_limit = 0;                     // > 0: cap on those slots (testing aid)
 
     // diagnostics
     unsigned long long *d_fp64_count = nullptr;

@@ -186,3 +186,39 @@ def test_pixel_map_at_nside_8192(cuda_device):
     ref = oracle.finalise(oracle.aperture_pixels_f32(oracle.pix2vec(nside, tg), nside, G1, G2, W, S2, n_p, 2,
                                                      2.0 * ARCMIN), 2.0 * ARCMIN)
     _check(got, ref, "nside 8192")
+
+
+def test_guard_band_targets_finished_in_place(cuda_device):
+    """Targets of the general kernel with guard-band pairs take slots that a
+    follow-up kernel finishes; a target that finds no free slot finishes
+    itself with the same code.  The aperture radius is set to the chord
+    between pixels three apart on polar ring 20 of NSIDE 64, so every target
+    on that ring has pairs inside the float32 guard band: with one slot, all
+    but one of them take the in-place path, and the maps stay bit-identical."""
+    nside, ring = 64, 20
+    z = 1.0 - ring * ring / (3.0 * nside * nside)
+    rho = math.sqrt((1.0 - z) * (1.0 + z))
+    theta_arcmin = 2.0 * math.asin(rho * math.sin(3 * (2 * math.pi / (4 * ring)) / 2)) / ARCMIN
+    dec_ring = math.degrees(math.asin(z))
+    cat = catalog(21, 60_000, 30.0, dec_ring, 8.0)
+    tg = cap_targets(nside, 30.0, dec_ring, 5.0)
+    on_ring = [p for p in tg if oracle.pix_info(nside, int(p))[0] == ring]
+    assert len(on_ring) >= 4
+    dev = cuda_device
+    ctx = api.Context(nside, theta_arcmin, "schirmer", nside_bin=nside)
+    c = cat.to(dev)
+    ctx.set_targets(torch.from_numpy(tg).to(dev))
+    ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+    a = ctx.map_pixel()
+    ctx.sync(60)
+    n_fp64 = ctx.fp64_decisions()
+    assert n_fp64 >= 2 * len(on_ring)
+    ctx.set_band_slot_limit(1)
+    b = ctx.map_pixel()
+    ctx.sync(60)
+    assert ctx.fp64_decisions() == n_fp64
+    for k in ("map_e", "map_b", "var", "sum_w", "count", "members"):
+        assert torch.equal(a[k], b[k]), k
+    ctx.set_band_slot_limit(0)
+    _, rpx = _oracle_maps(cat, tg, nside, nside, theta_arcmin, 2)
+    _check(a, rpx, "guard band")
