@@ -66,5 +66,6 @@ def test_stateless_calls_reject_bad_arguments():
     assert lib.smart_ang2pix(64, None, None, 0, None, None) == 0      # empty input is fine
     assert lib.smart_pix2vec(64, None, 3, None, None) == 1
     assert lib.smart_sync(None, 1.0) == 1
+    assert lib.smart_set_band_slot_limit(None, 1) == 1
     assert lib.smart_last_error(None) == b"null context"
     lib.smart_destroy(None)
