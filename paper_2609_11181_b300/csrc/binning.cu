@@ -127,16 +127,30 @@ template <typename T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict__ in, int64_t n_in,
                                                            int32_t *__restrict__ out, int64_t n,
                                                            int32_t *__restrict__ sums) {
+    static_assert(SCAN_ITEMS == 8, "two 16-byte words per thread");
     __shared__ int32_t ws[SCAN_THREADS / 32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    // a thread's 8 items are 32 contiguous bytes: two 16-byte loads and
+    // stores when both arrays are 16-byte aligned and the items are all in
+    // range (every thread but those of the last tile)
+    const bool vec = sizeof(T) == 4 && ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0 &&
+                     base + SCAN_ITEMS <= n_in && base + SCAN_ITEMS <= n;
     int32_t v[SCAN_ITEMS];
+    if (vec) {
+        const int4 p = __ldg(reinterpret_cast<const int4 *>(in + base));
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(in + base) + 1);
+        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+        v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            const int64_t i = base + k;
+            v[k] = i < n_in ? (int32_t)in[i] : 0;
+        }
+    }
     int32_t acc = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        const int64_t i = base + k;
-        v[k] = i < n_in ? (int32_t)in[i] : 0;
-        acc += v[k];
-    }
+    for (int k = 0; k < SCAN_ITEMS; ++k) acc += v[k];
     // inclusive scan of per-thread totals across the block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t x = acc;
@@ -158,11 +172,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict_
     }
     __syncthreads();
     int32_t run = x - acc + (warp > 0 ? ws[warp - 1] : 0);
+    if (vec) {
+        int32_t o[SCAN_ITEMS];
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        const int64_t i = base + k;
-        if (i < n) out[i] = run;
-        run += v[k];
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            o[k] = run;
+            run += v[k];
+        }
+        reinterpret_cast<int4 *>(out + base)[0] = make_int4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<int4 *>(out + base)[1] = make_int4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            const int64_t i = base + k;
+            if (i < n) out[i] = run;
+            run += v[k];
+        }
     }
     if (threadIdx.x == SCAN_THREADS - 1 && sums) sums[blockIdx.x] = run;
 }
