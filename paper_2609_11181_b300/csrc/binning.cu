@@ -45,6 +45,103 @@ __global__ void k_keys(int64_t N, const double *__restrict__ ra, const double *_
     }
 }
 
+// The same pixel from float32 arithmetic when that decision is certain, else
+// -1.  Every floor of the float64 definition (ang2pix64) is taken here on a
+// float32 value whose error is bounded: the azimuth in quarter turns t to
+// 9e-7 (ra rounded to float32 for |ra| < 720, the reduction to [0, 360) and
+// the division), |sin|, |cos| of the latitude to 6e-7 (argument rounding + 2
+// ulp of sincosf); hence the equatorial arguments N (1/2 + t) -+ (3/4) N z to
+// 2.2e-6 N, the polar t_p N cos(dec) sqrt(3 / (1 + |z|)) and its complement
+// to 2.6e-6 N and t i to 1.2e-6 N.  A value nearer an integer than about
+// twice its bound, a latitude near |z| = 2/3 or the poles, an azimuth near
+// the 0/360 seam or an input outside the plain range returns -1, and the
+// float64 definition decides; elsewhere its floors cannot differ.
+__device__ __forceinline__ int64_t ang2pix_certain(int64_t N, double ra, double dec) {
+    const float raf = (float)ra, df = (float)dec;
+    if (!(fabsf(raf) < 720.0f) || !(fabsf(df) < 89.99f)) return -1;        // NaN fails too
+    const float af = raf - 360.0f * floorf(raf * (1.0f / 360.0f));
+    if (!(af > 1e-3f && af < 359.999f)) return -1;
+    const float tt = af * (1.0f / 90.0f);
+    float sz, cz;
+    sincosf(df * 0.0174532925f, &sz, &cz);
+    const float za = fabsf(sz);
+    if (fabsf(za - 2.0f / 3.0f) < 4e-6f) return -1;
+    const float fN = (float)N;
+    if (za < 2.0f / 3.0f) {
+        const float tol = 5e-6f * fN;
+        const float t1 = fN * (0.5f + tt), t2 = 0.75f * fN * sz;
+        const float v1 = t1 - t2, v2 = t1 + t2;
+        const float f1 = floorf(v1), f2 = floorf(v2);
+        if (v1 - f1 < tol || f1 + 1.0f - v1 < tol || v2 - f2 < tol || f2 + 1.0f - v2 < tol) return -1;
+        const int64_t jp = (int64_t)f1, jm = (int64_t)f2;
+        const int64_t ir = N + 1 + jp - jm;
+        const int64_t kshift = 1 - (ir & 1);
+        int64_t ip = (jp + jm - N + kshift + 1) / 2;
+        ip = ((ip % (4 * N)) + 4 * N) % (4 * N);
+        return 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
+    }
+    const float tol = 6e-6f * fN;
+    const float tp = tt - floorf(tt);
+    const float tmp = fN * cz * sqrtf(3.0f / (1.0f + za));
+    const float v1 = tp * tmp, v2 = (1.0f - tp) * tmp;
+    const float f1 = floorf(v1), f2 = floorf(v2);
+    if (v1 - f1 < tol || f1 + 1.0f - v1 < tol || v2 - f2 < tol || f2 + 1.0f - v2 < tol) return -1;
+    const int64_t ir = (int64_t)f1 + (int64_t)f2 + 1;
+    const float v3 = tt * (float)ir;
+    const float f3 = floorf(v3);
+    const float tol3 = 3e-6f * fN;
+    if (v3 - f3 < tol3 || f3 + 1.0f - v3 < tol3) return -1;
+    int64_t ip = (int64_t)f3;
+    ip = ((ip % (4 * ir)) + 4 * ir) % (4 * ir);
+    if (sz > 0.0f) return 2 * ir * (ir - 1) + ip;
+    return 12 * N * N - 2 * ir * (ir + 1) + ip;
+}
+
+// keys of the catalogue: float32 where certain; the rest (with any input
+// outside the plain range) are listed, warp-aggregated, for k_keys_fix, which
+// checks the input and applies the float64 definition
+__global__ void k_keys_fast(int64_t N, const double *__restrict__ ra, const double *__restrict__ dec, int64_t n,
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *__restrict__ defer,
+                            unsigned long long *__restrict__ n_defer) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double a = ra[k], d = dec[k];
+        uint32_t key = 0;
+        bool need = false;
+        const int64_t p = ang2pix_certain(N, a, d);     // -1 also for inputs outside the plain range
+        need = p < 0;
+        key = need ? 0u : (uint32_t)p;
+        keys[k] = key;
+        vals[k] = (uint32_t)k;
+        const unsigned act = __activemask();
+        const unsigned m = __ballot_sync(act, need);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long b = 0;
+            if (lane == leader) b = atomicAdd(n_defer, (unsigned long long)__popc(m));
+            b = __shfl_sync(act, b, leader);
+            if (need) defer[b + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+        }
+    }
+}
+
+__global__ void k_keys_fix(int64_t N, const double *__restrict__ ra, const double *__restrict__ dec,
+                           uint32_t *__restrict__ keys, const uint32_t *__restrict__ defer,
+                           const unsigned long long *__restrict__ n_defer, int *__restrict__ invalid) {
+    const unsigned long long nd = *n_defer;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nd;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t k = defer[i];
+        const double a = ra[k], d = dec[k];
+        if (isfinite(a) && isfinite(d) && d >= -90.0 && d <= 90.0 && fabs(a) < 1e12) {
+            keys[k] = (uint32_t)ang2pix64(N, a, d);
+        } else {
+            keys[k] = (uint32_t)(12 * N * N);     // sentinel bucket after every real pixel
+            atomicAdd(invalid, 1);
+        }
+    }
+}
+
 // ------------------------------------------------------- radix passes
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                             int64_t ntiles, uint32_t *__restrict__ hist) {
@@ -370,8 +467,14 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     cudaMemsetAsync(c->d_invalid, 0, sizeof(int), s);
     if (n > 0) {
         {
+            // vals_alt and the radix histogram are free until the radix passes:
+            // they hold the galaxies left to float64 and their count
             KernelTimer timer(c, SMART_KT_BIN_KEYS);
-            k_keys<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, c->keys, c->vals, c->d_invalid);
+            unsigned long long *n_defer = reinterpret_cast<unsigned long long *>(c->hist);
+            cudaMemsetAsync(n_defer, 0, sizeof(unsigned long long), s);
+            k_keys_fast<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, c->keys, c->vals, c->vals_alt, n_defer);
+            k_keys_fix<<<(unsigned)(c->num_sms * 8), 256, 0, s>>>(N, ra, dec, c->keys, c->vals_alt, n_defer,
+                                                                   c->d_invalid);
         }
         if ((st = check_cuda(c, cudaGetLastError(), "k_keys")) != SMART_OK) return st;
         uint32_t *ki = c->keys, *ko = c->keys_alt, *vi = c->vals, *vo = c->vals_alt;
