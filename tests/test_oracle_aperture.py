@@ -10,7 +10,9 @@ independent evaluation of the paper's printed spherical formulas.
     mirror, a general rigid rotation, constant shear;
   * the flat-sky limit: gnomonic-plane estimator on the equator, O(theta_ap^2);
   * pixel mode equals brute force on the catalogue snapped to pixel centres;
-  * binning equals numpy's stable argsort / bincount.
+  * binning equals numpy's stable argsort / bincount;
+  * the noise map (Eq. 8) equals the Monte Carlo variance of M_E and M_B
+    under pure shape noise.
 """
 import math
 
@@ -513,3 +515,63 @@ def test_jarvis_q_follows_from_its_compensated_u():
         inner, _ = quad(lambda t: t * _u_jarvis(t, s), 0, x, epsabs=1e-14, epsrel=1e-12)
         q_from_u = 2.0 / (x * x) * inner - _u_jarvis(x, s)
         assert abs(oracle.filter_q(3, x, s) - q_from_u) < 1e-10 * max(1.0, abs(q_from_u))
+
+
+# ------------------------------------------- noise map normalisation (Eq. 8)
+def _noise_field(seed, theta_ap, per_target=600):
+    """Fixed positions and weights around centres whose apertures do not
+    overlap: pixel centres of an NSIDE 4 grid (spacing about 15 degrees) plus
+    one aperture around each pole, so that polar geometry is in the sample."""
+    rng = np.random.default_rng(seed)
+    cen = oracle.pix2vec(4, np.arange(0, 192, 4))
+    cen = np.concatenate([cen, oracle.radec2vec([17.0, 250.0], [89.93, -89.9])])
+    ra, dec = [], []
+    for c in cen:
+        # uniform in a cap of radius 1.05 theta_ap about c
+        cr = 1.0 - rng.random(per_target) * (1.0 - math.cos(1.05 * theta_ap))
+        sr = np.sqrt(1.0 - cr * cr)
+        ph = 2 * math.pi * rng.random(per_target)
+        a = np.array([0.0, 0.0, 1.0]) if abs(c[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+        e_1 = np.cross(a, c)
+        e_1 /= np.linalg.norm(e_1)
+        e_2 = np.cross(c, e_1)
+        v = cr[:, None] * c + sr[:, None] * (np.cos(ph)[:, None] * e_1 + np.sin(ph)[:, None] * e_2)
+        ra.append(np.degrees(np.arctan2(v[:, 1], v[:, 0])) % 360)
+        dec.append(np.degrees(np.arcsin(np.clip(v[:, 2], -1, 1))))
+    ra, dec = np.concatenate(ra), np.concatenate(dec)
+    w = rng.uniform(0.5, 1.5, ra.size)
+    return cen, ra, dec, w, rng
+
+
+@pytest.mark.parametrize("mode", ["galaxies", "pixels"])
+def test_noise_map_normalisation_monte_carlo(mode):
+    """Eq. 8 with weights: the noise map is the variance of M_E and M_B under
+    pure shape noise.  With e1, e2 ~ N(0, s^2) independent, E|e|^2 = 2 s^2,
+    so for fixed positions and weights Var(M_E) = Var(M_B) = (A / sum w)^2
+    sum w^2 Q^2 s^2, which is the expectation of sigma^2 = SV / (2 nbar^2).
+    The test draws many noise realisations through the oracle and compares
+    the pooled sample second moment of M_E and M_B (mean zero) with the
+    pooled mean of the oracle's sigma^2; a wrong factor 1/2, a w in place of
+    w^2, or nbar in place of nbar^2 moves the ratio far from 1.  M_E and M_B
+    are independent here (zero covariance, jointly Gaussian), so about
+    2 x 50 x 400 samples fix the ratio to about 0.7 % (one sd).  Pixel mode
+    bins each realisation (Sect. 3.2 step 2), so its S2 = sum w^2 |e|^2
+    holds noise of the same expectation."""
+    th = 20 * ARCMIN
+    cen, ra, dec, w, rng = _noise_field(11, th)
+    s = synth.SIGMA_E
+    m2, var = 0.0, 0.0
+    nreal = 400
+    for _ in range(nreal):
+        e1 = rng.normal(0.0, s, ra.size)
+        e2 = rng.normal(0.0, s, ra.size)
+        if mode == "galaxies":
+            r = oracle.map_galaxies(cen, ra, dec, e1, e2, w, 1, th)
+        else:
+            b = oracle.bin_catalog(256, ra, dec, e1, e2, w)
+            r = oracle.map_pixels(cen, 256, b["G1"], b["G2"], b["W"], b["S2"], b["n"], 1, th)
+        assert np.all(r["N"] > 100)
+        m2 += np.sum(r["ME"] ** 2 + r["MB"] ** 2)
+        var += 2.0 * np.sum(r["VAR"])
+    ratio = m2 / var
+    assert abs(ratio - 1.0) < 0.04, ratio
