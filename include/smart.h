@@ -455,7 +455,9 @@ smart_status smart_mlp_set_state(smart_mlp *h, const void *buf, int64_t size);
  * about 10.5 MB in the library's own device data, held by every GPU that
  * loads the library until the process exits.  The first call on each device
  * looks up that array's device address with that device current; make that
- * first call before any stream capture.  All calls share the array, and it
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: after cudaDeviceReset (or a reset of the primary context) it
+ * is stale, and the entry point must not be called again in that process.  All calls share the array, and it
  * keeps the last call's contents: calls that overlap on the GPU (on two
  * streams, or from two host threads, without ordering between them) race and
  * give wrong results.  The work is enqueued on the stream and the call

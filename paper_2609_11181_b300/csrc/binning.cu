@@ -255,10 +255,13 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint32_t *
 }
 
 // ------------------------------------------------------------- scan
-// exclusive scan of uint32/int32 counts (totals < 2^31), reduce-then-scan
+// exclusive scan of uint32/int32 counts (totals < 2^31), reduce-then-scan.
+// in and out may be the same array (the block sums and the allocation-free
+// sort scan in place): every item is read and then written by the same
+// thread, so in and out carry no no-alias promise and are read with plain
+// loads.
 template <typename T>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict__ in, int64_t n_in,
-                                                           int32_t *__restrict__ out, int64_t n,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *in, int64_t n_in, int32_t *out, int64_t n,
                                                            int32_t *__restrict__ sums) {
     static_assert(SCAN_ITEMS == 8, "two 16-byte words per thread");
     __shared__ int32_t ws[SCAN_THREADS / 32];
@@ -270,8 +273,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const T *__restrict_
                      base + SCAN_ITEMS <= n_in && base + SCAN_ITEMS <= n;
     int32_t v[SCAN_ITEMS];
     if (vec) {
-        const int4 p = __ldg(reinterpret_cast<const int4 *>(in + base));
-        const int4 q = __ldg(reinterpret_cast<const int4 *>(in + base) + 1);
+        const int4 p = reinterpret_cast<const int4 *>(in + base)[0];
+        const int4 q = reinterpret_cast<const int4 *>(in + base)[1];
         v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
         v[4] = q.x; v[5] = q.y; v[6] = q.z; v[7] = q.w;
     } else {
@@ -699,12 +702,15 @@ extern "C" smart_status smart_sort_catalog_noalloc(int nside, const double *ra, 
     uint32_t *hist = (uint32_t *)(scr + NOALLOC_HIST_OFF);
     int32_t *hscan = (int32_t *)(scr + NOALLOC_HSCAN_OFF);
     int32_t *tmp = (int32_t *)(scr + NOALLOC_SCAN_OFF);
-    int *invalid = (int *)(scr + NOALLOC_FLAG_OFF);      // counted but never read
+    int *invalid = (int *)(scr + NOALLOC_FLAG_OFF);      // counted but never read; cleared per call
     int bits = 0;
     while (((int64_t)1 << bits) <= npix) ++bits;          // keys go up to npix (sentinel)
-    // the per-pixel counts are accumulated in place in offsets and must start
-    // at zero; every other scratch word is written before it is read
-    if (cudaMemsetAsync(offsets, 0, (size_t)(npix + 1) * sizeof(int32_t), s) != cudaSuccess) return SMART_E_CUDA;
+    // the per-pixel counts are accumulated in place in offsets and the
+    // invalid-coordinate counter in the scratch: both start at zero on every
+    // call; every other scratch word is written before it is read
+    if (cudaMemsetAsync(offsets, 0, (size_t)(npix + 1) * sizeof(int32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(invalid, 0, sizeof(int), s) != cudaSuccess)
+        return SMART_E_CUDA;
     if (n > 0) {
         const int64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
         k_keys<<<grid_for(n, 256), 256, 0, s>>>(N, ra, dec, n, pix, perm, invalid);

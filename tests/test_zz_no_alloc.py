@@ -11,18 +11,21 @@ The GPU test runs it twice in a row on different catalogues (the second
 smaller and at another NSIDE, so anything the first call left in the shared
 array would show) and requires the result of each call to equal, bit for
 bit, the sort of the context path (smart_bin_galaxies + smart_get_catalog).
-The file is named so that pytest collects it last; it passes alone in a
+A second test sorts points placed on the pixel boundaries and compares the
+keys with the oracle's ang2pix.  The file is named so that pytest collects it last; it passes alone in a
 fresh process and after the other tests.
 """
 import ctypes
 
+import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2609_11181_b300 import _native as N
 from paper_2609_11181_b300 import api
 
-from _cases import catalog
+from _cases import boundary_points, catalog
 
 MAX_GALAXIES = 1 << 20
 SMART_E_ARG, SMART_E_OVERFLOW = 1, 6
@@ -57,7 +60,8 @@ def test_noalloc_sort_matches_context_sort_twice(cuda_device):
     stream = torch.cuda.current_stream().cuda_stream
     cases = [
         # (nside, catalogue): the first at the size limit with an odd number of
-        # radix passes (22-bit keys), the second smaller with four passes
+        # radix passes (24-bit keys, three passes), the second smaller with
+        # four passes
         (1024, catalog(71, MAX_GALAXIES, 30.0, 10.0, 8.0, nhalo=4, clumped=True)),
         (2048, catalog(72, 200_001, 210.0, -50.0, 3.0, nhalo=3)),
     ]
@@ -70,6 +74,25 @@ def test_noalloc_sort_matches_context_sort_twice(cuda_device):
         assert torch.equal(perm.long(), ref_perm), f"nside {nside}: permutation differs"
         assert torch.equal(off.long(), ref_off), f"nside {nside}: offsets differ"
         assert int(off[-1]) == ra.numel()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nside", [256, 8192])
+def test_noalloc_keys_at_pixel_boundaries(cuda_device, nside):
+    # this entry point computes every key with the float64 definition, the
+    # context path with float32 where that is certain: on points placed at
+    # every kind of pixel boundary both equal the oracle's ang2pix
+    lib = N.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    ra, dec = boundary_points(nside, 40_000, nside + 1)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(cuda_device, torch.float64)
+    pix, perm, off = _noalloc_sort(lib, nside, t(ra), t(dec), stream)
+    torch.cuda.synchronize()
+    ref = oracle.ang2pix(nside, ra, dec)
+    ref_perm = np.argsort(ref, kind="stable")
+    np.testing.assert_array_equal(pix.cpu().numpy().astype(np.int64), ref[ref_perm])
+    np.testing.assert_array_equal(perm.cpu().numpy().astype(np.int64), ref_perm)
+    np.testing.assert_array_equal(off.cpu().numpy()[ref[ref_perm]], np.searchsorted(ref[ref_perm], ref[ref_perm]))
 
 
 def test_noalloc_sort_rejects_bad_sizes():
