@@ -76,6 +76,12 @@ def lib():
         L.orc_aperture_points.argtypes = [i64, ip, i64, ip, ip, ip, ip, ip, ip,
                                           ctypes.c_int, dbl, dbl,
                                           ip, ip, ip, ip, ip, ip]
+        L.orc_project.argtypes = [dbl, dbl, i64, ip, ip, ip]
+        L.orc_plane_shear.argtypes = [dbl, dbl, i64, ip, ip, ip, ip, ip]
+        L.orc_aperture_projected.argtypes = [i64, ip, i64, ip, ip, ip, ip, ip, dbl, dbl,
+                                             ctypes.c_int, dbl, dbl, ip, ip, ip, ip, ip]
+        L.orc_finalise_area.argtypes = [i64, dbl, ip, ip, ip, ip, ip, ip, ip]
+        L.orc_annulus_stats.argtypes = [i64, ip, ip, dbl, ip, ip, i64, ip, ip, ip]
         _lib = L
     return _lib
 
@@ -343,6 +349,71 @@ def map_barycentre_averaged(centres, nside_bin, ra, dec, e1, e2, w, kind, theta_
     f = _avg_scale(nside_bin, b["W"][p])
     return _averaged(aperture_points(centres, bc["vec"], b["G1"][p] * f, b["G2"][p] * f, b["W"][p],
                                      b["S2"][p] * f * f, b["n"][p], kind, theta_ap, xc))
+
+
+# --------------------------------------------------------------------------
+# Cartesian (projected) estimator, projS_pos (Sect. 2.2, Sect. 5.2.1), and the
+# equal-area annulus statistics of Sect. 5.2.2
+# --------------------------------------------------------------------------
+def project(ra_c: float, dec_c: float, vec):
+    """Gnomonic plane coordinates (n, 2) about (ra_c, dec_c) of unit vectors
+    (n, 3), and a flag per point (False: no image, r . c <= 0)."""
+    v = _f64(vec).reshape(-1, 3)
+    xy = np.empty((v.shape[0], 2))
+    ok = np.empty(v.shape[0], dtype=np.int64)
+    lib().orc_project(float(ra_c), float(dec_c), v.shape[0], _p(v), _p(xy), _p(ok))
+    return xy, ok.astype(bool)
+
+
+def plane_shear(ra_c: float, dec_c: float, ra, dec, e1, e2) -> np.ndarray:
+    """Shear components (n, 2) in the plane's axes, rotated with the local
+    North (Sect. 2.2.2)."""
+    ra, dec, e1, e2 = (_f64(a).ravel() for a in (ra, dec, e1, e2))
+    g = np.empty((ra.size, 2))
+    lib().orc_plane_shear(float(ra_c), float(dec_c), ra.size, _p(ra), _p(dec), _p(e1), _p(e2), _p(g))
+    return g
+
+
+def aperture_projected(centres, ra, dec, e1, e2, w, ra_c, dec_c, kind, theta_ap, xc=0.15):
+    """Cartesian brute-force sums at unit-vector centres (projS_pos)."""
+    c = _f64(centres).reshape(-1, 3)
+    ra, dec, e1, e2, w = (_f64(a).ravel() for a in (ra, dec, e1, e2, w))
+    n0, n = c.shape[0], ra.size
+    SE, SB, SV, SW = (np.empty(n0) for _ in range(4))
+    N = np.empty(n0, dtype=np.int64)
+    lib().orc_aperture_projected(n0, _p(c), n, _p(ra), _p(dec), _p(e1), _p(e2), _p(w), float(ra_c), float(dec_c),
+                                 int(kind), float(xc), float(theta_ap), _p(SE), _p(SB), _p(SV), _p(SW), _p(N))
+    return dict(SE=SE, SB=SB, SV=SV, SW=SW, N=N)
+
+
+def finalise_area(sums: dict, area: float) -> dict:
+    """Summed normalisation with aperture area `area` (sr)."""
+    SE, SB, SV, SW = (_f64(sums[k]) for k in ("SE", "SB", "SV", "SW"))
+    n0 = SE.size
+    ME, MB, VAR = (np.empty(n0) for _ in range(3))
+    lib().orc_finalise_area(n0, float(area), _p(SE), _p(SB), _p(SV), _p(SW), _p(ME), _p(MB), _p(VAR))
+    out = dict(sums)
+    out.update(ME=ME, MB=MB, VAR=VAR)
+    return out
+
+
+def map_projected(centres, ra, dec, e1, e2, w, ra_c, dec_c, kind, theta_ap, xc=0.15):
+    """projS_pos map (Sect. 5.2.1): plane sums normalised with A = pi theta_ap^2."""
+    return finalise_area(aperture_projected(centres, ra, dec, e1, e2, w, ra_c, dec_c, kind, theta_ap, xc),
+                         np.pi * theta_ap * theta_ap)
+
+
+def annulus_stats(centres, ref_vec, rmax: float, m_x, m_ref, nbins: int):
+    """Equal-area annuli about ref_vec out to rmax (rad): count, mean and
+    population sd of (m_x - m_ref) / sd(m_ref) per annulus (Sect. 5.2.2)."""
+    c = _f64(centres).reshape(-1, 3)
+    r = _f64(ref_vec).ravel()
+    mx, mr = _f64(m_x).ravel(), _f64(m_ref).ravel()
+    cnt = np.empty(nbins, dtype=np.int64)
+    mean, sd = np.empty(nbins), np.empty(nbins)
+    lib().orc_annulus_stats(c.shape[0], _p(c), _p(r), float(rmax), _p(mx), _p(mr), int(nbins), _p(cnt), _p(mean),
+                            _p(sd))
+    return dict(count=cnt, mean=mean, sd=sd)
 
 
 def rms_rel(a, b) -> float:

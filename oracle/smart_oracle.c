@@ -22,6 +22,8 @@
  *   Sect. 3.1 steps 1-5                        brute force (sphS_pos)
  *   Sect. 3.2 steps 1-5                        pixel-based (sphS_pix)
  *   Sect. 3.4 steps 1-3                        sorted catalogue + offsets
+ *   Sect. 2.2.1, 2.2.2, Sect. 5.2.1 steps 1-4  Cartesian (projected) estimator
+ *   Sect. 5.2.2                                equal-area annulus statistics
  */
 #include <math.h>
 #include <stdint.h>
@@ -771,5 +773,239 @@ void orc_bin_catalog(int64_t nside, int64_t n, const double *ra,
         }
         G1[p] = g1; G2[p] = g2; W[p] = ww; S2[p] = s2;
         np[p] = offsets[p + 1] - offsets[p];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Cartesian (projected) shear-based estimator, projS_pos              */
+/* (Sect. 2.2, Sect. 5.2.1 steps 1-4).                                */
+/*                                                                    */
+/* Step 1: galaxy positions go to the plane tangent at the reference  */
+/* point c (gnomonic projection, Sect. 2.2.1).  With r the point's     */
+/* unit vector and (e_c, n_c) the East and North unit vectors at c,    */
+/* the printed numerators and denominator are dot products:            */
+/*   cos(d) sin(a - a_c)                         = r . e_c             */
+/*   cos(d_c) sin(d) - sin(d_c) cos(d) cos(a-a_c) = r . n_c            */
+/*   sin(d) sin(d_c) + cos(d) cos(d_c) cos(a-a_c) = r . c              */
+/* so x = (r . e_c) / (r . c), y = (r . n_c) / (r . c), in this order  */
+/* of operations: dot products summed ((0 + 1) + 2), then one division.*/
+/* Points with r . c <= 0 have no image and are left out.              */
+/* The shear is rotated with the basis (Sect. 2.2.2): its orientation  */
+/* is kept relative to the local North, whose image direction in the   */
+/* plane is the projection's differential applied to the galaxy's      */
+/* North unit vector t:  N = ((t.e_c) P - X (t.c), (t.n_c) P - Y (t.c))*/
+/* (up to the positive factor 1/P^2), with X, Y, P the three dot       */
+/* products above.  If rho is the angle from the plane's +y axis to N  */
+/* (counter-clockwise), gamma_plane = gamma e^{2 i rho}.               */
+/* Step 2: the target pixel centres go to the same plane.              */
+/* Step 3: per pair, separation (dx, dy) = galaxy - target in the      */
+/* plane, member iff dx^2 + dy^2 <= theta_ap^2, Q of the plane distance,*/
+/* phi = polar angle of (dx, dy); gamma_+ = -Re(gamma e^{-2 i phi}),   */
+/* gamma_x = -Im(gamma e^{-2 i phi}) (the same sign convention as the  */
+/* spherical sums; a member at the target itself carries no shear).   */
+/* Step 4: sums SE, SB, SV, SW, N as in the spherical brute force; the */
+/* normalisation is orc_finalise_area with A = pi theta_ap^2, the      */
+/* area of the aperture in the plane.                                  */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double c[3], e[3], n[3];
+} orc_plane;
+
+static void plane_setup(double ra_c, double dec_c, orc_plane *pl)
+{
+    double sa, ca, sd, cd;
+    orc_sincos_deg(ra_c, &sa, &ca);
+    orc_sincos_deg(dec_c, &sd, &cd);
+    pl->c[0] = cd * ca; pl->c[1] = cd * sa; pl->c[2] = sd;
+    pl->e[0] = -sa;     pl->e[1] = ca;      pl->e[2] = 0.0;
+    pl->n[0] = -sd * ca; pl->n[1] = -sd * sa; pl->n[2] = cd;
+}
+
+static double dot3(const double *a, const double *b)
+{
+    return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+/* plane coordinates of unit vector r; returns 0 when r has no image */
+static int plane_xy(const orc_plane *pl, const double *r, double *x, double *y)
+{
+    double P = dot3(r, pl->c);
+    if (!(P > 0.0)) return 0;
+    *x = dot3(r, pl->e) / P;
+    *y = dot3(r, pl->n) / P;
+    return 1;
+}
+
+void orc_project(double ra_c, double dec_c, int64_t n, const double *v, double *xy, int64_t *ok)
+{
+    orc_plane pl;
+    plane_setup(ra_c, dec_c, &pl);
+    for (int64_t k = 0; k < n; ++k) {
+        double x = 0.0, y = 0.0;
+        ok[k] = plane_xy(&pl, v + 3 * k, &x, &y);
+        xy[2 * k] = x;
+        xy[2 * k + 1] = y;
+    }
+}
+
+/* the shear of a galaxy at (ra, dec) in the plane's axes (Sect. 2.2.2) */
+static void plane_shear(const orc_plane *pl, double ra, double dec, double e1, double e2,
+                        double *g1, double *g2)
+{
+    double sa, ca, sd, cd;
+    orc_sincos_deg(ra, &sa, &ca);
+    orc_sincos_deg(dec, &sd, &cd);
+    double r[3] = {cd * ca, cd * sa, sd};
+    double t[3] = {-sd * ca, -sd * sa, cd};          /* local North */
+    double P = dot3(r, pl->c), X = dot3(r, pl->e), Y = dot3(r, pl->n);
+    double Nx = dot3(t, pl->e) * P - X * dot3(t, pl->c);
+    double Ny = dot3(t, pl->n) * P - Y * dot3(t, pl->c);
+    double nn = Nx * Nx + Ny * Ny;
+    double c2 = (Ny * Ny - Nx * Nx) / nn;            /* cos 2 rho */
+    double s2 = -2.0 * Nx * Ny / nn;                 /* sin 2 rho */
+    *g1 = e1 * c2 - e2 * s2;
+    *g2 = e1 * s2 + e2 * c2;
+}
+
+void orc_plane_shear(double ra_c, double dec_c, int64_t n, const double *ra, const double *dec,
+                     const double *e1, const double *e2, double *g)
+{
+    orc_plane pl;
+    plane_setup(ra_c, dec_c, &pl);
+    for (int64_t k = 0; k < n; ++k) plane_shear(&pl, ra[k], dec[k], e1[k], e2[k], g + 2 * k, g + 2 * k + 1);
+}
+
+void orc_aperture_projected(int64_t n0, const double *c, int64_t n,
+                            const double *ra, const double *dec,
+                            const double *e1, const double *e2, const double *w,
+                            double ra_c, double dec_c, int kind, double xc, double theta_ap,
+                            double *SE, double *SB, double *SV, double *SW, int64_t *N)
+{
+    orc_plane pl;
+    plane_setup(ra_c, dec_c, &pl);
+    double Tp = theta_ap * theta_ap;
+    /* per galaxy: unit vector, plane position, plane shear; or no image */
+    double *gv = (double *)malloc(sizeof(double) * 7 * (size_t)(n > 0 ? n : 1));
+    double *zi = (double *)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        double *g = gv + 7 * k;
+        orc_radec2vec(ra[k], dec[k], g);
+        g[5] = 0.0;
+        if (plane_xy(&pl, g, g + 3, g + 4)) {
+            plane_shear(&pl, ra[k], dec[k], e1[k], e2[k], g + 5, g + 6);
+        } else {
+            g[3] = 0.0; g[4] = 0.0; g[6] = 0.0;
+            g[5] = NAN;                                 /* marks "no image" */
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        zi[2 * k] = gv[7 * k + 2];
+        zi[2 * k + 1] = (double)k;
+    }
+    qsort(zi, (size_t)n, 2 * sizeof(double), cmp_dbl_idx);
+    /* a member in the plane is within theta_ap on the sphere too (the plane
+       distance of two images is at least their great-circle distance), so
+       |z - z0| <= theta_ap bounds the candidates */
+    double band = theta_ap * (1.0 + 1e-9) + 1e-15;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n0; ++t) {
+        const double *r0 = c + 3 * t;
+        double x0, y0;
+        double se = 0, sb = 0, sv = 0, sw = 0;
+        int64_t cnt = 0;
+        if (plane_xy(&pl, r0, &x0, &y0)) {
+            double zlo = r0[2] - band, zhi = r0[2] + band;
+            int64_t lo = 0, hi = n;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) / 2;
+                if (zi[2 * mid] < zlo) lo = mid + 1; else hi = mid;
+            }
+            for (int64_t m = lo; m < n && zi[2 * m] <= zhi; ++m) {
+                int64_t k = (int64_t)zi[2 * m + 1];
+                const double *g = gv + 7 * k;
+                if (isnan(g[5])) continue;
+                double dx = g[3] - x0, dy = g[4] - y0;
+                double q = dx * dx + dy * dy;
+                if (!(q <= Tp)) continue;
+                double qv = orc_filter_q(kind, xc, sqrt(q) / theta_ap) / Tp;
+                double c2 = 0.0, s2 = 0.0;                 /* cos 2 phi, sin 2 phi */
+                if (q > 0.0) {
+                    c2 = (dx * dx - dy * dy) / q;
+                    s2 = 2.0 * dx * dy / q;
+                }
+                double gp = -(g[5] * c2 + g[6] * s2);      /* gamma_+ */
+                double gx = g[5] * s2 - g[6] * c2;         /* gamma_x */
+                se += w[k] * gp * qv;
+                sb += w[k] * gx * qv;
+                sv += w[k] * w[k] * (e1[k] * e1[k] + e2[k] * e2[k]) * qv * qv;
+                sw += w[k];
+                cnt += 1;
+            }
+        }
+        SE[t] = se; SB[t] = sb; SV[t] = sv; SW[t] = sw; N[t] = cnt;
+    }
+    free(gv);
+    free(zi);
+}
+
+/* summed normalisation with a given aperture area A (sr):
+   nbar = SW / A, M = S / nbar, sigma^2 = SV / (2 nbar^2) */
+void orc_finalise_area(int64_t n0, double A, const double *SE, const double *SB,
+                       const double *SV, const double *SW, double *ME, double *MB, double *VAR)
+{
+    for (int64_t t = 0; t < n0; ++t) {
+        if (SW[t] > 0.0) {
+            double nbar = SW[t] / A;
+            ME[t] = SE[t] / nbar;
+            MB[t] = SB[t] / nbar;
+            VAR[t] = SV[t] / (2.0 * nbar * nbar);
+        } else {
+            ME[t] = 0.0; MB[t] = 0.0; VAR[t] = 0.0;
+        }
+    }
+}
+
+/*
+ * Equal-area annulus statistics about a reference point (Sect. 5.2.2): the
+ * targets (unit vectors c) are binned by their angular distance d from the
+ * reference unit vector r_ref into nbins annuli of equal area out to rmax
+ * (annulus k holds 1 - cos d in [k, k + 1) (1 - cos rmax) / nbins); per
+ * annulus the count, and the mean and population standard deviation of
+ * eps = (mx - mref) / sref are returned, where sref is the population
+ * standard deviation of mref over all the given targets (Eq. 12).  Targets
+ * beyond rmax are ignored; empty annuli give zeros.
+ */
+void orc_annulus_stats(int64_t n0, const double *c, const double *r_ref, double rmax,
+                       const double *mx, const double *mref, int64_t nbins,
+                       int64_t *count, double *mean, double *sd)
+{
+    double m = 0.0;
+    for (int64_t t = 0; t < n0; ++t) m += mref[t];
+    m /= (double)(n0 > 0 ? n0 : 1);
+    double v = 0.0;
+    for (int64_t t = 0; t < n0; ++t) v += (mref[t] - m) * (mref[t] - m);
+    double sref = sqrt(v / (double)(n0 > 0 ? n0 : 1));
+    double cmax = 1.0 - cos(rmax);
+    for (int64_t k = 0; k < nbins; ++k) { count[k] = 0; mean[k] = 0.0; sd[k] = 0.0; }
+    for (int64_t t = 0; t < n0; ++t) {
+        const double *p = c + 3 * t;
+        /* 1 - cos d from the chord: 1 - cos d = s^2 / 2 */
+        double dx = p[0] - r_ref[0], dy = p[1] - r_ref[1], dz = p[2] - r_ref[2];
+        double u = 0.5 * ((dx * dx + dy * dy) + dz * dz);
+        if (!(u < cmax)) continue;
+        int64_t k = (int64_t)floor(u / cmax * (double)nbins);
+        if (k >= nbins) k = nbins - 1;
+        double e = (mx[t] - mref[t]) / sref;
+        count[k] += 1;
+        mean[k] += e;
+        sd[k] += e * e;
+    }
+    for (int64_t k = 0; k < nbins; ++k) {
+        if (count[k] == 0) continue;
+        double mu = mean[k] / (double)count[k];
+        double var = sd[k] / (double)count[k] - mu * mu;
+        mean[k] = mu;
+        sd[k] = sqrt(var > 0.0 ? var : 0.0);
     }
 }
