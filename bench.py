@@ -5,7 +5,10 @@
 
 Default workload (N=1): the NSIDE-4096 pixel-based map over a 15,000 deg^2
 cap (binned shear given per pixel, Schirmer filter x_c = 0.15, theta_ap =
-10').  A step is one full pixel-based map: register the binned input and run
+10').  After the headline, the default single-GPU run also times the other
+forms of the metric at their own configurations (brute force over 5e7
+galaxies, 64 maps in one batched launch, the learned correction and the
+barycentre form) and reports them under "forms"; --no-forms skips them.  A step is one full pixel-based map: register the binned input and run
 the aperture kernel (geometry, membership, rotation, filter, compensated sums
 and the summed normalisation all happen in that launch).  The metric is
 pairs per second (Gpair/s) -- a pair is one (target pixel, pixel whose
@@ -41,13 +44,26 @@ sys.path.insert(0, ROOT)
 from paper_2609_11181_b300 import api, workloads  # noqa: E402
 
 METRIC = "NSIDE-4096 M_ap map time & Gpair/s, chosen vs plain form at <=1e-4 rel err"
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12     # 148 SMs x 128 FP32 lanes x FMA x 2032 MHz
-# float32 flops per member pair in k_map_pixel (counted from the source, FMA = 2,
-# each library transcendental = 1): lattice offset 2, sin/haversine series 15,
-# chord 2, tangent-plane direction + cos/sin 2psi 10, chord->separation series 9,
-# Schirmer filter 15, weight 1, E/B 10, variance + weight 4.
-FLOPS_PER_PAIR = {"schirmer": 68, "poly": 56}
-PEAK_SOURCE = "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (recipe unit counts and maximum SM clock)"
+FP32_NOMINAL_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12     # 148 SMs x 128 FP32 lanes x FMA x 2032 MHz
+# Algorithmic float32 work of one member pair in the direct form of the method
+# (FMA = 2 flop): the ring-pair geometry with no sqrt, divide or trig (azimuth
+# offset, sine and haversine of it, chord^2 = A + B h, tangent-plane direction
+# x, y), cos 2psi and sin 2psi from x and y, the filter weight, the rotation
+# into gamma_+ and gamma_x, and the E, B, variance and weight sums: about 45
+# flop for the polynomial filter; a tabulated filter (Schirmer, Jarvis) adds
+# one reciprocal square root and a cubic table lookup (about 9 more).
+ALGO_FLOPS_PER_PAIR = {"poly": 45, "schirmer": 54, "jarvis": 54}
+# Executed float32 work per pair of the Toeplitz kernel: geometry, filter and
+# rotation are tabulated once per ring pair and index offset and shared by
+# every target, so a pair costs 4 FMAs for E and B, 1 FMA for the variance and
+# one add for the weight.
+TOEPLITZ_EXEC_FLOPS_PER_PAIR = 11
+# Executed float32 work per pair of the general pixel kernel, counted from its
+# pair body (FMA = 2): lattice offset 2, sine / haversine series 15, chord 2,
+# tangent-plane direction and cos / sin 2psi 10, filter 15 (Schirmer table) or
+# 9 + 3 (chord-to-separation series + polynomial), weight 1, E / B 10, variance
+# and weight sums 4.
+GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 68, "jarvis": 68, "poly": 56}
 
 
 def _env_int(k, d):
@@ -194,29 +210,76 @@ def profiled_traffic(kernel: str, workload: str):
         return None
 
 
+def measure_fma_peaks(stream, target_ms=60.0, repeats=3):
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s), measured with the
+    library's probe kernel (eight FMA chains per thread, 8 CTAs of 256
+    threads per SM) timed with CUDA events on `stream`; best of `repeats`
+    launches of about target_ms each after a warm-up.  Changes no clock or
+    power setting."""
+    out = {}
+    for bits in (32, 64):
+        iters = 512 if bits == 32 else 16
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        while True:                                   # size the launch to about target_ms
+            a.record(stream)
+            flops = api.fma_probe(bits, iters, 8, stream)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            if ms >= 0.25 * target_ms or iters > (1 << 26):
+                break
+            iters *= 4
+        iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+        best = 0.0
+        for _ in range(repeats):
+            a.record(stream)
+            flops = api.fma_probe(bits, iters, 8, stream)
+            b.record(stream)
+            b.synchronize()
+            best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
+        out[f"fp{bits}_tflops"] = round(best, 3)
+    out["how"] = ("library probe smart_fma_probe: 8 independent FMA chains per thread, 8 x 256-thread CTAs per SM, "
+                  f"about {target_ms:.0f} ms per launch, best of {repeats} (CUDA events)")
+    out["fp32_nominal_tflops"] = round(FP32_NOMINAL_TFLOPS, 2)
+    return out
+
+
 def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_source: str):
     """Roofline of the dominant kernel from the context's per-launch events.
 
-    kernels: {name: (pairs per launch, flops per pair, kernel symbol)}.  The
-    dominant kernel is the one with the largest summed time over the timed
-    steps; achieved = algorithmic flops per launch / its mean launch time."""
+    kernels: {name: (pairs per launch, algorithmic flops per pair, executed
+    flops per pair, kernel symbol)}.  The dominant kernel is the one with the
+    largest summed time over the timed steps; achieved = algorithmic flops per
+    launch (the direct-form count per pair x member pairs) / its mean launch
+    time, or the executed flops where they are fewer (a kernel that shares
+    work between pairs, the Toeplitz kernel, is held to what it executes).
+    Both are reported per kernel."""
     per = {}
-    for name, (pairs, fpp, sym) in kernels.items():
+    for name, (pairs, fpp, exec_fpp, sym) in kernels.items():
         n, ms = ctx.timing_read(name)
         if n == 0:
             continue
+        t = ms / n * 1e-3
         per[name] = {"kernel": sym, "launches": n, "total_ms": round(ms, 3), "ms_per_launch": round(ms / n, 4),
-                     "pairs_per_launch": int(pairs), "flops_per_pair": fpp,
-                     "tflops": round(pairs * fpp / (ms / n * 1e-3) / 1e12, 2) if ms > 0 else None}
+                     "pairs_per_launch": int(pairs), "gpair_s": round(pairs / t / 1e9, 2) if t > 0 else None,
+                     "algorithmic_flops_per_pair": fpp, "executed_flops_per_pair": exec_fpp,
+                     "algorithmic_tflops": round(pairs * fpp / t / 1e12, 2) if t > 0 and fpp else None,
+                     "executed_tflops": round(pairs * exec_fpp / t / 1e12, 2) if t > 0 and exec_fpp else None}
     if not per:
         return None, per
     dom = max(per, key=lambda k: per[k]["total_ms"])
     d = per[dom]
-    achieved = d["tflops"]
+    if d["executed_flops_per_pair"] is None or d["algorithmic_flops_per_pair"] <= d["executed_flops_per_pair"]:
+        achieved, basis = d["algorithmic_tflops"], "algorithmic flops (direct form per pair)"
+    else:
+        # a kernel that shares work between pairs is held to what it executes
+        achieved, basis = d["executed_tflops"], "executed flops (work shared between pairs)"
     roof = {"bound": "alu", "achieved": achieved, "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
             "frac": round(achieved / peak_tflops, 4), "traffic": profiled_traffic(d["kernel"], workload),
             "kernel": d["kernel"], "launches": d["launches"], "ms_per_launch": d["ms_per_launch"],
-            "pairs_per_launch": d["pairs_per_launch"], "flops_per_pair": d["flops_per_pair"],
+            "pairs_per_launch": d["pairs_per_launch"],
+            "algorithmic_flops_per_pair": d["algorithmic_flops_per_pair"],
+            "executed_flops_per_pair": d["executed_flops_per_pair"], "achieved_basis": basis,
             "peak_source": peak_source}
     return roof, per
 
@@ -224,8 +287,9 @@ def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_
 # ---------------------------------------------------------------------------
 # CPU baseline: the float64 oracle on a bounded sample of the same targets
 # ---------------------------------------------------------------------------
-def cpu_baseline_pixel(wl, G, budget_s=15.0, seed=0):
-    """G: host copies of (G1, G2, W, S2, n)."""
+def cpu_baseline_pixel(wl, G, budget_s=15.0, seed=0, return_sample=False):
+    """G: host copies of (G1, G2, W, S2, n).  With return_sample, also the
+    sampled targets and the oracle's sums for them."""
     import oracle
     tg = wl.targets.cpu().numpy()
     rng = np.random.default_rng(seed)
@@ -238,32 +302,85 @@ def cpu_baseline_pixel(wl, G, budget_s=15.0, seed=0):
         cv = oracle.pix2vec(wl.nside, s)
         t0 = time.perf_counter()
         r = oracle.aperture_pixels_f32(cv, wl.nside, *G, kind, th)
-        return time.perf_counter() - t0, int(r["NPIX"].sum()), s.size
+        return time.perf_counter() - t0, int(r["NPIX"].sum()), s.size, (s, r)
 
     m = max(256, cores * 64)
-    dt, pairs, m = run(m)
+    dt, pairs, m, sr = run(m)
     while dt < 0.25 * budget_s and m < tg.size:          # grow until the timing is meaningful
         m = int(min(tg.size, m * max(2.0, 0.5 * budget_s / max(dt, 1e-3))))
-        dt, pairs, m = run(m)
-    return {"value": pairs / dt / 1e9, "unit": "Gpair/s", "cores": cores, "kind": "oracle",
-            "sample": f"{m} random targets of {tg.size} (float64 oracle, OpenMP over targets), {pairs} pairs, "
-                      f"{dt:.1f} s"}, pairs, dt, m
+        dt, pairs, m, sr = run(m)
+    cb = {"value": pairs / dt / 1e9, "unit": "Gpair/s", "cores": cores, "kind": "oracle",
+          "sample": f"{m} random targets of {tg.size} (float64 oracle, OpenMP over targets), {pairs} pairs, "
+                    f"{dt:.1f} s"}
+    if return_sample:
+        return cb, pairs, dt, m, sr
+    return cb, pairs, dt, m
+
+
+def accuracy_vs_oracle(out: dict, targets: np.ndarray, sample: np.ndarray, ref: dict, theta_ap: float,
+                       tol: float = 1e-4) -> dict:
+    """The map at the sampled targets against the float64 oracle's sums for
+    them: counts bit-exact, rms(M - M_oracle) / rms(M_oracle) for M_E, M_B
+    and sigma^2, largest relative error of the weight sum."""
+    import oracle
+    idx = np.searchsorted(targets, sample)
+    assert np.array_equal(targets[idx], sample)
+    ref = oracle.finalise(ref, theta_ap)
+    it = torch.from_numpy(idx).to(out["map_e"].device)
+    got = {k: v[it].cpu().numpy() for k, v in out.items()}
+    rr = {k: oracle.rms_rel(got[g].astype(np.float64), ref[o])
+          for k, g, o in (("map_e", "map_e", "ME"), ("map_b", "map_b", "MB"), ("var", "var", "VAR"))}
+    sw = float(np.max(np.abs(got["sum_w"] - ref["SW"]) / np.maximum(np.abs(ref["SW"]), 1e-300)))
+    counts = bool(np.array_equal(got["count"], ref["N"]))
+    if "members" in got and "NPIX" in ref:
+        counts = counts and bool(np.array_equal(got["members"], ref["NPIX"]))
+    return {"targets": int(sample.size), "counts_bit_exact": counts,
+            "rms_rel": {k: float(f"{v:.3e}") for k, v in rr.items()}, "sum_w_max_rel": float(f"{sw:.3e}"),
+            "tolerance": tol, "within_tolerance": counts and all(v <= tol for v in rr.values()) and sw <= 1e-6}
 
 
 PIXEL_WORKLOADS = workloads.PIXEL_WORKLOADS
 
 
+def _oracle_centres(nside, p):
+    """Pixel centres from the float64 oracle, for inputs that the oracle leg
+    also consumes (no oracle input may come from the CUDA path)."""
+    import oracle
+    return torch.from_numpy(oracle.pix2vec(nside, p.cpu().numpy())).to(p.device)
+
+
+def first_map_ms(wl, inputs, out):
+    """A one-shot caller's map: a fresh context, targets, the binned input and
+    one pixel map, synchronised (host clock around everything, so the
+    context's table set-up and its allocations are included)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = api.Context(wl.nside, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside)
+    c.set_targets(wl.targets)
+    c.set_binned_packed(*inputs)
+    c.map_pixel(out)
+    c.sync(300)
+    ms = (time.perf_counter() - t0) * 1e3
+    c.close()
+    return ms
+
+
 def run_native_pixel(args, world, rank):
     dev = torch.device("cuda", torch.cuda.current_device())
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    stream = torch.cuda.current_stream()
+    peaks_live = measure_fma_peaks(stream)
     t_gen = time.perf_counter()
-    wl = workloads.pixel_workload(dev, api.pix2vec, **PIXEL_WORKLOADS[args.workload])
+    # the oracle leg compares the map with float64 sums over the same inputs,
+    # so those inputs are generated with the oracle's pixel centres
+    wl = workloads.pixel_workload(dev, _oracle_centres if want_cpu else api.pix2vec,
+                                  **PIXEL_WORKLOADS[args.workload])
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     ctx = api.Context(wl.nside, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside)
     ctx.set_targets(wl.targets)
     n = wl.targets.numel()
     out = ctx._out(None)[0]
-    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     host_G = [x.cpu().numpy() for x in (wl.G1, wl.G2, wl.W, wl.S2, wl.n)] if want_cpu else None
     # the library's native input layout: (G1, G2, S2, W) per pixel + counts
     px = torch.stack([wl.G1, wl.G2, wl.S2, wl.W], dim=1).contiguous()
@@ -274,6 +391,10 @@ def run_native_pixel(args, world, rank):
         ctx.set_binned_packed(*inputs)
         ctx.map_pixel(out)
 
+    # a one-shot map first, on a fresh context (tables built, nothing cached)
+    scratch_out = ctx._out(None)[0]
+    first_ms = first_map_ms(wl, inputs, scratch_out)
+    del scratch_out
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -281,7 +402,6 @@ def run_native_pixel(args, world, rank):
     pairs_step = int(members.sum().item())
     gen_idx = ctx.general_targets()
     pairs_gen = int(members[gen_idx].sum().item()) if gen_idx.numel() else 0
-    stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(torch.cuda.current_device())
     barrier(world)
@@ -303,15 +423,21 @@ def run_native_pixel(args, world, rank):
     ms_step = max_over_ranks(total_ms / args.steps, world)
     pairs_all = sum_over_ranks(float(pairs_step), world)
     value = pairs_all / (ms_step * 1e-3) / 1e9
-    flops = FLOPS_PER_PAIR[wl.filter]
+    algo = ALGO_FLOPS_PER_PAIR[wl.filter]
+    peak = peaks_live["fp32_tflops"]
+    peak_src = (f"FP32 FMA throughput measured in this run by the library's probe ({peaks_live['how']}); "
+                f"nominal {FP32_NOMINAL_TFLOPS:.2f} (148 SMs x 128 lanes x 2 x 2032 MHz)")
     roof, per_kernel = kernel_roofline(
-        ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, flops, "k_pixel_toeplitz"),
-              "pixel_general": (pairs_gen, flops, "k_pixel_general"),
-              "pixel_band": (0, flops, "k_pixel_band")},
-        args.workload, FP32_PEAK_TFLOPS, PEAK_SOURCE)
+        ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, algo, TOEPLITZ_EXEC_FLOPS_PER_PAIR, "k_pixel_toeplitz"),
+              "pixel_general": (pairs_gen, algo, GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter], "k_pixel_general"),
+              "pixel_band": (0, None, None, "k_pixel_band")},
+        args.workload, peak, peak_src)
     ctx.timing(False)
     npix_bin = 12 * wl.nside ** 2
     launches_step = sum(v["launches"] for v in per_kernel.values()) / args.steps + scan_launches(npix_bin + 1)
+    map_roof = {"achieved": round(pairs_step * algo / (ms_step * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
+                "peak": peak, "frac": round(pairs_step * algo / (ms_step * 1e-3) / 1e12 / peak, 4),
+                "basis": f"whole step: member pairs x {algo} algorithmic flop per pair / ms_per_step"}
 
     # end to end through the public API: every step copies its inputs from
     # pinned host memory, maps them and reads all results back.  Steps are
@@ -366,6 +492,7 @@ def run_native_pixel(args, world, rank):
     torch.cuda.synchronize()
     same = all(torch.equal(host_out[(e_steps - 1) % 2][k].to(v.device), v) for k, v in out.items())
     ectx.close()
+    del dev_in, outs, host_out, host_in
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e_steps, world)
 
     peaks = load_peaks()
@@ -381,8 +508,11 @@ def run_native_pixel(args, world, rank):
                    "parallelism": f"replicas x{world}"},
         "map_time_ms": round(ms_step, 3),
         "step_ms_mean": round(kmean, 3),
+        "first_map_ms": round(first_ms, 3),
         "roofline": roof,
+        "map_roofline": map_roof,
         "kernels": per_kernel,
+        "fma_peaks_measured": peaks_live,
         "e2e": {"value": round(pairs_all / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gpair/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
                 "steps": e_steps, "pipelined": "double-buffered; copy in, map and copy out on three streams",
@@ -394,23 +524,31 @@ def run_native_pixel(args, world, rank):
     if peaks:
         res["measured_peaks_present"] = True
     if want_cpu:
-        cb, _, _, _ = cpu_baseline_pixel(wl, host_G)
+        cb, _, _, _, (smp, ref) = cpu_baseline_pixel(wl, host_G, return_sample=True)
         res["cpu_baseline"] = cb
+        res["accuracy"] = accuracy_vs_oracle(out, wl.targets.cpu().numpy(), smp, ref,
+                                             wl.theta_ap_arcmin * math.pi / 10800)
+        res["accuracy"]["of"] = "the timed map (last step) at the cpu_baseline sample of targets, float64 oracle"
     ctx.close()
+    del out, inputs, px
+    torch.cuda.empty_cache()
     return res
 
 
 GALAXY_WORKLOADS = workloads.GALAXY_WORKLOADS
-# float32 flops per member pair of the brute-force kernel (source count, FMA = 2):
-# offsets 2, latitude series 10, azimuth series 9, chord 3, direction + 2psi 10,
-# filter 8, weight 1, E/B 10, variance + weight 4
-BRUTE_FLOPS_PER_PAIR = {"poly": 57, "schirmer": 62}
+# executed float32 flops per member pair of the brute-force kernel (source
+# count, FMA = 2): offsets 2, latitude series 10, azimuth series 9, chord 3,
+# direction + 2psi 10, filter 8, weight 1, E/B 10, variance + weight 4
+BRUTE_EXEC_FLOPS_PER_PAIR = {"poly": 57, "schirmer": 62, "jarvis": 62}
 
 
-def run_native_galaxy(args, world, rank):
+def run_native_galaxy(args, world, rank, peaks_live=None, accuracy_targets=0):
     dev = torch.device("cuda", torch.cuda.current_device())
+    if peaks_live is None:
+        peaks_live = measure_fma_peaks(torch.cuda.current_stream())
     t_gen = time.perf_counter()
-    wl = workloads.galaxy_workload(dev, api.pix2vec, **GALAXY_WORKLOADS[args.workload])
+    wl = workloads.galaxy_workload(dev, _oracle_centres if accuracy_targets else api.pix2vec,
+                                   **GALAXY_WORKLOADS[args.workload])
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     ctx = api.Context(wl.nside_out, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside_bin)
@@ -455,9 +593,12 @@ def run_native_galaxy(args, world, rank):
     m_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in bin_ms)
     ms_step = max_over_ranks(total, world)
     value = sum_over_ranks(float(pairs_step), world) / (ms_step * 1e-3) / 1e9
-    flops = BRUTE_FLOPS_PER_PAIR[wl.filter]
-    roof, per_kernel = kernel_roofline(ctx, {"galaxy": (pairs_step, flops, "k_map_galaxy")}, args.workload,
-                                       FP32_PEAK_TFLOPS, PEAK_SOURCE)
+    peak = peaks_live["fp32_tflops"]
+    peak_src = (f"FP32 FMA throughput measured in this run by the library's probe ({peaks_live['how']}); "
+                f"nominal {FP32_NOMINAL_TFLOPS:.2f} (148 SMs x 128 lanes x 2 x 2032 MHz)")
+    roof, per_kernel = kernel_roofline(
+        ctx, {"galaxy": (pairs_step, ALGO_FLOPS_PER_PAIR[wl.filter], BRUTE_EXEC_FLOPS_PER_PAIR[wl.filter],
+                         "k_map_galaxy")}, args.workload, peak, peak_src)
     phases = {}
     for name in ("bin_keys", "bin_sort", "bin_records", "bin_pixel_sums", "galaxy_band", "galaxy_finalise"):
         nl, ms = ctx.timing_read(name)
@@ -480,9 +621,24 @@ def run_native_galaxy(args, world, rank):
                       "l2": "inputs (2.4 GB catalogue) larger than L2; no flush"},
            "bin_ms": round(b_ms, 3), "map_ms": round(m_ms, 3),
            "roofline": roof, "kernels": per_kernel, "phases": phases,
-           "gpu_launches": launches_step * args.steps,
+           "gpu_launches": launches_step * args.steps, "fma_peaks_measured": peaks_live,
            "clocks": ck, "input_gen_s": round(t_gen, 1)}
+    if accuracy_targets:
+        import oracle
+        tg = wl.targets.cpu().numpy()
+        smp = np.sort(np.random.default_rng(2048).choice(tg, min(accuracy_targets, tg.size), replace=False))
+        e1, e2, w = (x.double().cpu().numpy() for x in (cat.e1, cat.e2, cat.w))
+        t_o = time.perf_counter()
+        ref = oracle.aperture_galaxies(oracle.pix2vec(wl.nside_out, smp), cat.ra_deg.cpu().numpy(),
+                                       cat.dec_deg.cpu().numpy(), e1, e2, w, 1 if wl.filter == "poly" else 2,
+                                       wl.theta_ap_arcmin * math.pi / 10800)
+        t_o = time.perf_counter() - t_o
+        res["accuracy"] = accuracy_vs_oracle(out, tg, smp, ref, wl.theta_ap_arcmin * math.pi / 10800)
+        res["accuracy"]["of"] = (f"the timed map at {smp.size} random targets against the float64 oracle's sum "
+                                 f"over all {cat.n} galaxies ({t_o:.1f} s on the host)")
     ctx.close()
+    del out, cat, wl
+    torch.cuda.empty_cache()
     return res
 
 
@@ -718,6 +874,55 @@ def run_reference(args, world, rank):
             "e2e": {"value": round(v, 6), "unit": "Gpair/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_forms(args, world, rank, headline: dict) -> dict:
+    """The other forms of the metric ("chosen vs plain form"), each at its own
+    configuration, timed after the headline in the default run: brute force
+    at scale (5e7 galaxies), the batched persistent launch (64 maps), and the
+    learned correction with the barycentre form (220 catalogues).  A form
+    that fails records its error instead of a result."""
+    forms = {"plain_pixel": {"workload": headline["config"]["workload"], "ms_per_map": headline["ms_per_step"],
+                             "gpair_s": headline["value"], "accuracy_vs_oracle": headline.get("accuracy")}}
+    peaks_live = headline.get("fma_peaks_measured")
+
+    def leg(name, fn):
+        t0 = time.perf_counter()
+        try:
+            forms[name] = fn()
+        except Exception as e:                        # noqa: BLE001 -- recorded, the headline stands
+            forms[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        forms[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+
+    def brute():
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.steps, a.warmup = "brute2048", 3, 3
+        r = run_native_galaxy(a, world, rank, peaks_live=peaks_live, accuracy_targets=100)
+        return {"workload": "brute2048", "desc": r["config"]["desc"], "ms_per_step": r["ms_per_step"],
+                "bin_ms": r["bin_ms"], "map_ms": r["map_ms"], "gpair_s": r["value"],
+                "pairs_per_step": r["config"]["pairs_per_step"], "roofline": r["roofline"],
+                "accuracy_vs_oracle": r.get("accuracy"), "clocks": r["clocks"]}
+
+    def batched():
+        a = argparse.Namespace(**vars(args))
+        a.steps, a.warmup = 3, 3
+        r = run_native_batch(a, world, rank)
+        return {"workload": "batch64", "desc": r["config"]["desc"], "ms_per_step": r["ms_per_step"],
+                "sequential_ms_per_step": r["sequential_ms_per_step"], "batched_speedup": r["batched_speedup"],
+                "gpair_s": r["value"], "pairs_per_step": r["config"]["pairs_per_step"],
+                "batched_equals_sequential": r["batched_equals_sequential"], "autotune": r["autotune"],
+                "clocks": r["clocks"]}
+
+    def learned():
+        r = run_native_learned(args, world, rank)
+        return {"workload": "learned", "desc": r["config"]["desc"], "forms": r["forms"], "training": r["training"],
+                "network": r["config"]["network"]}
+
+    leg("brute_force", brute)
+    leg("batched", batched)
+    leg("learned", learned)
+    return forms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -729,6 +934,8 @@ def main():
     ap.add_argument("--train-maps", type=int, default=200)
     ap.add_argument("--eval-maps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other forms (brute force, batched, learned) after the headline")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -743,6 +950,8 @@ def main():
         res = run_native_galaxy(args, world, rank)
     else:
         res = run_native_pixel(args, world, rank)
+        if args.workload == "pixel4096" and world == 1 and not args.no_forms:
+            res["forms"] = run_forms(args, world, rank, res)
     if rank == 0 and res is not None:
         print(json.dumps(res), flush=True)
     if world > 1:

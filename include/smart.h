@@ -183,6 +183,49 @@ smart_status smart_map_pixel(smart_ctx *ctx, const smart_maps *out);
 smart_status smart_map_barycentre(smart_ctx *ctx, const smart_maps *out);
 
 /*
+ * Cartesian (projected) shear-based aperture mass at galaxy positions,
+ * projS_pos (Sect. 2.2; algorithm of Sect. 5.2.1 steps 1-4), over the
+ * catalogue of smart_bin_galaxies and the targets of smart_set_targets:
+ *  1. galaxies go to the plane tangent at the reference point (ra_c, dec_c)
+ *     (degrees) by the gnomonic projection of Sect. 2.2.1; their shear is
+ *     rotated so that its orientation stays relative to the local North
+ *     (Sect. 2.2.2); galaxies more than 90 degrees from the reference point
+ *     have no image and are left out;
+ *  2. the targets' pixel centres go to the same plane;
+ *  3. per target, every galaxy whose plane distance is <= theta_ap is a
+ *     member; Q is evaluated at the plane distance (same filter kinds as the
+ *     spherical maps), gamma_+ / gamma_x from the bearing in the plane;
+ *  4. the summed normalisation with A = pi theta_ap^2, the aperture's area
+ *     in the plane: M = A S / sum_w, sigma^2 = A^2 V / (2 sum_w^2).
+ * Membership is decided like the float64 definition (float32 outside a
+ * guard band, float64 inside it), so counts are exact.  Outputs as for
+ * smart_map_bruteforce (count = members = galaxies in the plane aperture);
+ * a target with no image gets zeros.  SMART_E_STATE without a catalogue or
+ * with the averaged normalisation (only the summed form is implemented),
+ * SMART_E_ARG for a bad reference point.  Asynchronous on the context
+ * stream; the catalogue must stay unchanged until it completes.
+ */
+smart_status smart_map_projected(smart_ctx *ctx, double ra_c_deg, double dec_c_deg, const smart_maps *out);
+
+/*
+ * Equal-area annulus statistics of two maps of this context's targets about
+ * a reference point (Sect. 5.2.2): with d the angular distance of a target's
+ * pixel centre from (ra_ref, dec_ref) (degrees), annulus k of nbins holds
+ * the targets with 1 - cos d in [k, k + 1) (1 - cos rmax_rad) / nbins --
+ * annuli of equal area out to rmax_rad (radians, in (0, pi]).  Per annulus:
+ * count[k] (int64), and the mean and population standard deviation of
+ * eps = (m_x - m_ref) / sigma(m_ref) (Eq. 12), sigma(m_ref) being the
+ * population standard deviation of m_ref over all the targets.  m_x, m_ref:
+ * float32 [n_targets], device; count, mean, sd: device arrays of nbins (any
+ * may be NULL).  Targets beyond rmax_rad are not binned.  Sums are float64
+ * atomics (order-dependent in the last bits).  Asynchronous on the context
+ * stream.  SMART_E_ARG for nbins outside [1, 2^20] or bad angles.
+ */
+smart_status smart_annulus_stats(smart_ctx *ctx, double ra_ref_deg, double dec_ref_deg, double rmax_rad,
+                                 const float *m_x, const float *m_ref, int nbins, int64_t *count,
+                                 double *mean, double *sd);
+
+/*
  * Normalisation of the maps of a context (Sect. 2.4).
  * SMART_NORM_SUMMED (default): M = A S / sum_w with A the aperture area,
  *   sigma^2 = A^2 V / (2 sum_w^2) (the paper's default form).
@@ -284,7 +327,10 @@ typedef enum {
     SMART_KT_BARY_BUILD = 9,       /* smart_map_barycentre: barycentre records (once per catalogue) */
     SMART_KT_BARY_MAP = 10,        /* smart_map_barycentre: main kernel */
     SMART_KT_PIXEL_BAND = 11,      /* pixel mode, float64 decisions of the general kernel's guard-band pairs */
-    SMART_KT_COUNT = 12
+    SMART_KT_PROJ_RECORDS = 12,    /* smart_map_projected: plane positions and rotated shears */
+    SMART_KT_PROJ_MAP = 13,        /* smart_map_projected: main kernel */
+    SMART_KT_PROJ_BAND = 14,       /* smart_map_projected: float64 decisions of guard-band pairs */
+    SMART_KT_COUNT = 15
 } smart_kernel_id;
 
 /*
@@ -311,6 +357,18 @@ smart_status smart_timing_read(smart_ctx *ctx, int kernel, int64_t *launches, do
  * map after smart_set_targets.  Asynchronous on the context stream.
  */
 smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_gen);
+
+/*
+ * FMA throughput probe (diagnostics; the paper has no counterpart).  Enqueues
+ * one kernel of ctas_per_sm (1..8) CTAs of 256 threads per SM on the stream;
+ * every thread runs iters x 128 fused multiply-adds in eight independent
+ * chains, in float32 (bits = 32) or float64 (bits = 64).  *flops (host)
+ * receives the kernel's floating-point operations (an FMA counts 2); the
+ * caller times the launch with events on the same stream and divides.
+ * Returns at once; SMART_E_ARG for bad arguments, SMART_E_CUDA on a launch
+ * failure.  Allocates nothing.
+ */
+smart_status smart_fma_probe(int bits, int64_t iters, int ctas_per_sm, void *cuda_stream, double *flops);
 
 /*
  * Testing aid (no counterpart in the paper).  In the pixel map, a target of

@@ -17,7 +17,7 @@ STATUS = {0: "SMART_OK", 1: "SMART_E_ARG", 2: "SMART_E_NOMEM", 3: "SMART_E_CUDA"
 
 KERNELS = {"pixel_toeplitz": 0, "pixel_general": 1, "galaxy": 2, "galaxy_band": 3, "galaxy_finalise": 4,
            "bin_keys": 5, "bin_sort": 6, "bin_records": 7, "bin_pixel_sums": 8, "bary_build": 9, "bary_map": 10,
-           "pixel_band": 11}
+           "pixel_band": 11, "proj_records": 12, "proj_map": 13, "proj_band": 14}
 
 MLP_FEATURES = 4
 MLP_NPARAMS = 4545
@@ -87,6 +87,9 @@ SIGNATURES = {
     "smart_mlp_get_state": (_I32, [_VP, _VP, _I64, ctypes.POINTER(_I64)]),
     "smart_mlp_set_state": (_I32, [_VP, _VP, _I64]),
     "smart_sort_catalog_noalloc": (_I32, [_I32, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "smart_fma_probe": (_I32, [_I32, _I64, _I32, _VP, ctypes.POINTER(_D)]),
+    "smart_map_projected": (_I32, [_VP, _D, _D, ctypes.POINTER(SmartMaps)]),
+    "smart_annulus_stats": (_I32, [_VP, _D, _D, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
 }
 
 _lib = None

@@ -61,6 +61,17 @@ def pix2vec(nside: int, pix: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def fma_probe(bits: int, iters: int, ctas_per_sm: int = 8, stream=None) -> float:
+    """Enqueue the FMA throughput probe (float32 or float64) on the stream and
+    return its floating-point operation count; time it with events."""
+    flops = ctypes.c_double(0.0)
+    st = N.load().smart_fma_probe(int(bits), int(iters), int(ctas_per_sm), _stream_handle(stream),
+                                  ctypes.byref(flops))
+    if st:
+        raise SmartError(st, "smart_fma_probe")
+    return flops.value
+
+
 class Context:
     """One aperture-mass problem: output grid, filter, aperture, bin grid."""
 
@@ -185,6 +196,29 @@ class Context:
         out, m = self._out(out)
         self._check(self._lib.smart_map_bruteforce(self._h, ctypes.byref(m)), "smart_map_bruteforce")
         return out
+
+    def map_projected(self, ra_c_deg: float, dec_c_deg: float, out: dict | None = None) -> dict:
+        """Cartesian (projected) map about the reference point (needs bin_galaxies)."""
+        out, m = self._out(out)
+        self._check(self._lib.smart_map_projected(self._h, float(ra_c_deg), float(dec_c_deg), ctypes.byref(m)),
+                    "smart_map_projected")
+        return out
+
+    def annulus_stats(self, ra_ref_deg: float, dec_ref_deg: float, rmax_rad: float, m_x: torch.Tensor,
+                      m_ref: torch.Tensor, nbins: int) -> dict:
+        """Equal-area annuli about the reference point: count, mean and sd of
+        (m_x - m_ref) / sd(m_ref) per annulus (device tensors)."""
+        n = self.n_targets
+        dev = m_x.device
+        count = torch.empty(nbins, dtype=torch.int64, device=dev)
+        mean = torch.empty(nbins, dtype=torch.float64, device=dev)
+        sd = torch.empty(nbins, dtype=torch.float64, device=dev)
+        self._check(self._lib.smart_annulus_stats(self._h, float(ra_ref_deg), float(dec_ref_deg), float(rmax_rad),
+                                                  _ptr(m_x, torch.float32, "m_x", n),
+                                                  _ptr(m_ref, torch.float32, "m_ref", n), int(nbins),
+                                                  _ptr(count, torch.int64, "count"), _ptr(mean, torch.float64, "mean"),
+                                                  _ptr(sd, torch.float64, "sd")), "smart_annulus_stats")
+        return dict(count=count, mean=mean, sd=sd)
 
     def sync(self, timeout_s: float = 0.0):
         self._check(self._lib.smart_sync(self._h, float(timeout_s)), "smart_sync")
