@@ -542,7 +542,72 @@ GALAXY_WORKLOADS = workloads.GALAXY_WORKLOADS
 BRUTE_EXEC_FLOPS_PER_PAIR = {"poly": 57, "schirmer": 62, "jarvis": 62}
 
 
-def run_native_galaxy(args, world, rank, peaks_live=None, accuracy_targets=0):
+def projected_leg(ctx, wl, cat, out_sph, steps, accuracy_targets):
+    """The Cartesian (projected) form, projS_pos, on the same catalogue and
+    targets: gnomonic projection about the cap centre, brute force in the
+    plane; its time, its accuracy against the float64 oracle, and the
+    equal-area annulus statistics of (projected - spherical) / sd(spherical)
+    against the distance from the projection centre (Sect. 5.2.2)."""
+    stream = torch.cuda.current_stream()
+    ra_c, dec_c = 0.0, 0.0
+    proj = ctx.map_projected(ra_c, dec_c)            # warm
+    torch.cuda.synchronize()
+    ctx.timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ctx.map_projected(ra_c, dec_c, proj)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    phases = {}
+    for name in ("proj_records", "proj_map", "proj_band"):
+        nl, t = ctx.timing_read(name)
+        if nl:
+            phases[name] = round(t / nl, 4)
+    ctx.timing(False)
+    pairs = int(proj["members"].long().sum().item())
+    radius = synth_cap_radius(1000.0)
+    nb = 10
+    st = ctx.annulus_stats(ra_c, dec_c, radius, proj["map_e"], out_sph["map_e"], nb)
+    torch.cuda.synchronize()
+    edges = [math.degrees(math.acos(1 - (k / nb) * (1 - math.cos(radius)))) for k in range(nb + 1)]
+    res = {"ms_per_map": round(ms, 3), "gpair_s": round(pairs / (ms * 1e-3) / 1e9, 3), "pairs": pairs,
+           "phases_ms": phases, "reference_point_deg": [ra_c, dec_c],
+           "annuli_vs_spherical": {"outer_radius_deg": [round(e, 3) for e in edges[1:]],
+                                   "count": st["count"].cpu().tolist(),
+                                   "eps_sd": [float(f"{v:.4e}") for v in st["sd"].cpu().tolist()],
+                                   "eps_mean": [float(f"{v:.4e}") for v in st["mean"].cpu().tolist()],
+                                   "of": "eps = (M_E projected - M_E spherical brute force) / sd(M_E spherical), "
+                                         "equal-area annuli about the projection centre"}}
+    if accuracy_targets:
+        import oracle
+        tg = wl.targets.cpu().numpy()
+        smp = np.sort(np.random.default_rng(2049).choice(tg, min(accuracy_targets, tg.size), replace=False))
+        e1, e2, w = (x.double().cpu().numpy() for x in (cat.e1, cat.e2, cat.w))
+        th = wl.theta_ap_arcmin * math.pi / 10800
+        ref = oracle.aperture_projected(oracle.pix2vec(wl.nside_out, smp), cat.ra_deg.cpu().numpy(),
+                                        cat.dec_deg.cpu().numpy(), e1, e2, w, ra_c, dec_c,
+                                        1 if wl.filter == "poly" else 2, th)
+        # the plane estimator's normalisation uses the plane area pi theta_ap^2
+        ref_n = oracle.finalise_area(ref, math.pi * th * th)
+        idx = np.searchsorted(tg, smp)
+        it = torch.from_numpy(idx).to(proj["map_e"].device)
+        got = {k: v[it].cpu().numpy() for k, v in proj.items()}
+        res["accuracy_vs_oracle"] = {
+            "targets": int(smp.size), "counts_bit_exact": bool(np.array_equal(got["count"], ref["N"])),
+            "rms_rel": {k: float(f"{oracle.rms_rel(got[g].astype(np.float64), ref_n[o]):.3e}")
+                        for k, g, o in (("map_e", "map_e", "ME"), ("map_b", "map_b", "MB"), ("var", "var", "VAR"))},
+            "tolerance": 1e-4}
+    return res
+
+
+def synth_cap_radius(area_deg2):
+    from paper_2609_11181_b300 import synth
+    return synth.cap_radius_for_area(area_deg2)
+
+
+def run_native_galaxy(args, world, rank, peaks_live=None, accuracy_targets=0, projected=False):
     dev = torch.device("cuda", torch.cuda.current_device())
     if peaks_live is None:
         peaks_live = measure_fma_peaks(torch.cuda.current_stream())
@@ -636,6 +701,8 @@ def run_native_galaxy(args, world, rank, peaks_live=None, accuracy_targets=0):
         res["accuracy"] = accuracy_vs_oracle(out, tg, smp, ref, wl.theta_ap_arcmin * math.pi / 10800)
         res["accuracy"]["of"] = (f"the timed map at {smp.size} random targets against the float64 oracle's sum "
                                  f"over all {cat.n} galaxies ({t_o:.1f} s on the host)")
+    if projected:
+        res["projected"] = projected_leg(ctx, wl, cat, out, args.steps, accuracy_targets)
     ctx.close()
     del out, cat, wl
     torch.cuda.empty_cache()
@@ -896,7 +963,9 @@ def run_forms(args, world, rank, headline: dict) -> dict:
     def brute():
         a = argparse.Namespace(**vars(args))
         a.workload, a.steps, a.warmup = "brute2048", 3, 3
-        r = run_native_galaxy(a, world, rank, peaks_live=peaks_live, accuracy_targets=100)
+        r = run_native_galaxy(a, world, rank, peaks_live=peaks_live, accuracy_targets=100, projected=True)
+        forms["projected"] = dict(r.pop("projected"), workload="brute2048 (same catalogue and targets)",
+                                  form="Cartesian projected estimator projS_pos (Sect. 2.2, 5.2.1)")
         return {"workload": "brute2048", "desc": r["config"]["desc"], "ms_per_step": r["ms_per_step"],
                 "bin_ms": r["bin_ms"], "map_ms": r["map_ms"], "gpair_s": r["value"],
                 "pairs_per_step": r["config"]["pairs_per_step"], "roofline": r["roofline"],
