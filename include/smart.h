@@ -17,10 +17,18 @@
  *    parameter says "host".  The caller keeps inputs alive until
  *    smart_sync() returns.
  *  - Calls run asynchronously on the context's CUDA stream (the stream
- *    given to smart_create, 0 = legacy default stream) and return at once,
- *    unless their description says that they wait (smart_sync with a
- *    deadline; smart_bin_galaxies and the table builders read one value
- *    back; the timing and MLP state calls copy to the host).
+ *    given to smart_create, 0 = legacy default stream) and return at once.
+ *    The map calls (smart_map_*), smart_bin_galaxies and smart_set_binned*
+ *    never wait for the GPU: errors that only the device can see (invalid
+ *    galaxy coordinates, a full guard-band list) are reported by the next
+ *    smart_sync.  smart_sync waits with its own deadline.  The set-up calls
+ *    that size tables from device results -- smart_set_targets (the ring
+ *    tables of every map kind are built there), smart_batch_create -- and
+ *    smart_last_fp64_decisions wait for the stream, polling, at most the
+ *    context's wait limit (smart_set_wait_limit, default 600 s); past it
+ *    they return SMART_E_TIMEOUT (or -1).  smart_timing_read waits with the
+ *    deadline it is given; the MLP parameter, scaler and state copies wait
+ *    for their handle's stream (smart_mlp_sync takes a deadline).
  *  - The library owns only its internal scratch (sorted catalogue, offsets,
  *    ring tables, binned maps it made itself) and frees it in
  *    smart_destroy().
@@ -111,10 +119,20 @@ const char *smart_last_error(const smart_ctx *ctx);
 
 /*
  * Target (output) pixels: n RING indices at nside_out, int64, device
- * pointer.  They must be sorted ascending and unique.  The array is copied;
- * the caller may free it after smart_sync.
+ * pointer.  They must be sorted ascending and unique (SMART_E_ARG if not).
+ * The array is copied; the caller may free it after smart_sync.  This call
+ * also builds every table the maps need for these targets (ring pairs and
+ * Toeplitz tables once per context; target tiles, the pixel map's ring
+ * classes and general-target list, the brute-force target groups), so it
+ * waits for the stream, at most the wait limit (SMART_E_TIMEOUT after it);
+ * the map calls then only enqueue kernels.
  */
 smart_status smart_set_targets(smart_ctx *ctx, const int64_t *ring_pix, int64_t n);
+
+/* Wait limit (seconds, >= 0; 0 = none) of the set-up calls' waits on this
+   context (smart_set_targets, smart_last_fp64_decisions).  Default 600.
+   SMART_E_ARG for a negative value.  Host only. */
+smart_status smart_set_wait_limit(smart_ctx *ctx, double seconds);
 
 /*
  * Sect. 3.4 steps 1-3 and Sect. 3.2 step 2: assign each galaxy its RING
@@ -125,9 +143,10 @@ smart_status smart_set_targets(smart_ctx *ctx, const int64_t *ring_pix, int64_t 
  *   n = count
  * in float32, accumulated in sorted order.  ra/dec: f64 degrees; e1, e2,
  * w: f32; all device pointers of n entries.  w may be NULL (all weights 1).
- * Replaces any binned map given earlier with smart_set_binned.  Waits for
- * the stream before returning: galaxies with non-finite ra/dec or
- * |dec| > 90 make it return SMART_E_ARG (the catalogue is then unusable).
+ * Replaces any binned map given earlier with smart_set_binned.  Does not
+ * wait: galaxies with non-finite ra/dec or |dec| > 90 are sorted after every
+ * pixel and left out of the catalogue and the binned map (they belong to no
+ * pixel), and the next smart_sync returns SMART_E_ARG with their number.
  */
 smart_status smart_bin_galaxies(smart_ctx *ctx, const double *ra_deg,
                                 const double *dec_deg, const float *e1,
@@ -308,7 +327,8 @@ smart_status smart_get_binned(smart_ctx *ctx, float *G1, float *G2, float *W,
                               float *S2, int32_t *n_p);
 
 /* Number of member tests that fell inside the float32 guard band and were
-   decided in float64 by the last map call (host value; syncs the stream). */
+   decided in float64 by the last map call (host value; waits for the
+   stream at most the wait limit; -1 on a timeout or error). */
 int64_t smart_last_fp64_decisions(smart_ctx *ctx);
 
 /* ---- kernel timing (diagnostics; not part of the method) ------------ */

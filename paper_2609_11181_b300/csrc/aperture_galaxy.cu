@@ -25,9 +25,9 @@
 
 namespace smart {
 
-constexpr int GT = 4;              // targets per warp
+constexpr int GT_LOG2 = GAL_GROUP_LOG2;
+constexpr int GT = 1 << GT_LOG2;   // targets per warp
 constexpr int GW = 8;              // warps per CTA
-constexpr int GT_LOG2 = 2;
 
 struct GalRing {
     int start, nr;
@@ -407,9 +407,10 @@ __global__ void k_bary_wr(int64_t n, const double2 *__restrict__ radec, const fl
 // one thread per record: the pixel's w r added in catalogue order (one
 // addition at a time), normalised; the unit vector and the float32 offsets
 // from the pixel centre are written
-__global__ void k_bary_vec(int64_t N, int64_t nrec, const uint32_t *__restrict__ keys,
+__global__ void k_bary_vec(int64_t N, const int32_t *__restrict__ nrec_dev, const uint32_t *__restrict__ keys,
                            const int32_t *__restrict__ off, const double *__restrict__ wr,
                            const double *__restrict__ lat_deg, float4 *__restrict__ geo, double *__restrict__ vec) {
+    const int64_t nrec = *nrec_dev;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrec; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = keys[r];
         const int32_t a = off[p], b = off[p + 1];
@@ -455,31 +456,25 @@ static smart_status build_barycentres(smart_ctx *c) {
         if ((st = check_cuda(c, cudaGetLastError(), "k_bary_flags")) != SMART_OK) return st;
         if ((st = exclusive_scan_i32(c, c->np_prefix, c->bary_off, npix, npix + 1)) != SMART_OK) return st;
     }
-    int32_t nb = 0;
-    if ((st = check_cuda(c, cudaMemcpyAsync(&nb, c->bary_off + npix, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
-                         "barycentre count")) != SMART_OK)
-        return st;
-    if ((st = check_cuda(c, cudaStreamSynchronize(s), "barycentre count")) != SMART_OK) return st;
-    const int64_t need = std::max<int64_t>(nb, 1);
+    // records: one per pixel holding galaxies, at most one per galaxy; sized
+    // by that bound so that the count need not be read back (the kernels
+    // take it from bary_off[npix] on the device)
+    const int64_t need = std::max<int64_t>(std::min<int64_t>(c->n_gal, npix), 1);
     if (need > c->cap_bary) {
-        void *bufs[] = {c->bary_geo, c->bary_sh, c->bary_keys, c->bary_cnt, c->bary_vec};
-        for (void *b : bufs)
-            if (b) cudaFree(b);
-        c->bary_geo = c->bary_sh = nullptr;
-        c->bary_keys = nullptr;
-        c->bary_cnt = nullptr;
-        c->bary_vec = nullptr;
-        c->cap_bary = 0;
-        if (cudaMalloc(&c->bary_geo, need * sizeof(float4)) != cudaSuccess ||
-            cudaMalloc(&c->bary_sh, need * sizeof(float4)) != cudaSuccess ||
-            cudaMalloc(&c->bary_keys, need * sizeof(uint32_t)) != cudaSuccess ||
-            cudaMalloc(&c->bary_cnt, need * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&c->bary_vec, 3 * need * sizeof(double)) != cudaSuccess)
-            return fail(c, SMART_E_NOMEM, "cudaMalloc(barycentre records) failed");
+        void **bufs[] = {(void **)&c->bary_geo, (void **)&c->bary_sh, (void **)&c->bary_keys, (void **)&c->bary_cnt,
+                         (void **)&c->bary_vec};
+        const size_t elem[] = {sizeof(float4), sizeof(float4), sizeof(uint32_t), sizeof(int32_t), 3 * sizeof(double)};
+        for (int k = 0; k < 5; ++k) {
+            int64_t have = *bufs[k] ? c->cap_bary : 0;
+            if ((st = ensure_alloc(c, bufs[k], have, need, elem[k], "barycentre records")) != SMART_OK) {
+                c->cap_bary = 0;
+                return st;
+            }
+        }
         c->cap_bary = need;
     }
-    c->n_bary = nb;
-    if (nb > 0) {
+    c->n_bary = need;          // an upper bound of the records
+    if (c->n_gal > 0) {
         // w r of every galaxy: float64 scratch of 24 bytes per galaxy
         st = ensure_alloc(c, (void **)&c->bary_wr, c->cap_bary_wr, 3 * c->n_gal, sizeof(double), "barycentre scratch");
         if (st != SMART_OK) return st;
@@ -487,9 +482,9 @@ static smart_status build_barycentres(smart_ctx *c) {
         k_bary_keys<<<g, 256, 0, s>>>(npix, c->bary_off, c->own_px, c->own_np, c->bary_sh, c->bary_keys, c->bary_cnt);
         const unsigned gw = (unsigned)std::min<int64_t>((c->n_gal + 255) / 256, (int64_t)c->num_sms * 32);
         k_bary_wr<<<gw, 256, 0, s>>>(c->n_gal, c->rec_radec, c->rec_shear, c->bary_wr);
-        const unsigned gv = (unsigned)std::min<int64_t>((nb + 127) / 128, (int64_t)c->num_sms * 32);
-        k_bary_vec<<<gv, 128, 0, s>>>(N, nb, c->bary_keys, c->offsets, c->bary_wr, c->ring_lat, c->bary_geo,
-                                      c->bary_vec);
+        const unsigned gv = (unsigned)std::min<int64_t>((need + 127) / 128, (int64_t)c->num_sms * 32);
+        k_bary_vec<<<gv, 128, 0, s>>>(N, c->bary_off + npix, c->bary_keys, c->offsets, c->bary_wr, c->ring_lat,
+                                      c->bary_geo, c->bary_vec);
     }
     if ((st = check_cuda(c, cudaGetLastError(), "barycentre records")) != SMART_OK) return st;
     c->bary_version = c->catalog_version;

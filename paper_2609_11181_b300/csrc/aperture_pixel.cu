@@ -256,10 +256,10 @@ smart_status build_tiles_log2(smart_ctx *c, int log2_slots, int64_t **tiles, int
     k_tile_flags<<<blocks, 256, 0, c->stream>>>(c->targets, n, c->nside_out, log2_slots, flag);
     st = exclusive_scan_i32(c, flag, idx, n, n);
     if (st != SMART_OK) return st;
-    int32_t last[2] = {0, 0};
+    int32_t *last = reinterpret_cast<int32_t *>(c->host_rb);
     cudaMemcpyAsync(&last[0], idx + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(&last[1], flag + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
-    st = check_cuda(c, cudaStreamSynchronize(c->stream), "tile count");
+    st = wait_stream(c, "tile count");
     if (st != SMART_OK) return st;
     const int64_t nt = (int64_t)last[0] + last[1];
     st = ensure_alloc(c, (void **)tiles, *cap, nt + 1, sizeof(int64_t), "tiles");
@@ -316,13 +316,27 @@ __device__ double table_Q_of_chord(int kind, double s, double xc, double theta_a
     return n * q;
 }
 
-__global__ void k_filter_table(int kind, double xc, double theta_ap, double sap, float4 *__restrict__ tab) {
+// Q and dQ/dr at plane distance r (Cartesian estimator: Q of the distance itself)
+__device__ double table_Q_of_plane(int kind, double r, double xc, double theta_ap, double *dQ) {
+    double dq;
+    const double q = kind == SMART_FILTER_JARVIS ? jarvis_q(r / theta_ap, xc, &dq) : schirmer_q(r / theta_ap, xc, &dq);
+    const double n = 1.0 / (theta_ap * theta_ap);
+    *dQ = n * dq / theta_ap;
+    return n * q;
+}
+
+// cubic pieces of Q on [0, sap] in QTAB_BINS uniform bins of the chord
+// (plane = 0, sap = chord of theta_ap) or of the plane distance (plane = 1,
+// sap = theta_ap)
+__global__ void k_filter_table(int kind, double xc, double theta_ap, double sap, int plane, float4 *__restrict__ tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= QTAB_BINS) return;
     const double h = sap / QTAB_BINS;
     double d0, d1;
-    const double q0 = table_Q_of_chord(kind, i * h, xc, theta_ap, &d0);
-    const double q1 = table_Q_of_chord(kind, (i + 1) * h, xc, theta_ap, &d1);
+    const double q0 = plane ? table_Q_of_plane(kind, i * h, xc, theta_ap, &d0)
+                            : table_Q_of_chord(kind, i * h, xc, theta_ap, &d0);
+    const double q1 = plane ? table_Q_of_plane(kind, (i + 1) * h, xc, theta_ap, &d1)
+                            : table_Q_of_chord(kind, (i + 1) * h, xc, theta_ap, &d1);
     d0 *= h;
     d1 *= h;
     // Hermite cubic on t in [0, 1]: q0 + d0 t + c2 t^2 + c3 t^3
@@ -331,27 +345,33 @@ __global__ void k_filter_table(int kind, double xc, double theta_ap, double sap,
     tab[i] = make_float4((float)q0, (float)d0, (float)c2, (float)c3);
 }
 
-smart_status ensure_filter_table(smart_ctx *c) {
-    if (c->filter_kind == SMART_FILTER_POLY || c->qtab) return SMART_OK;
-    if (cudaMalloc(&c->qtab, QTAB_BINS * sizeof(float4)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(filter table) failed");
-    k_filter_table<<<(QTAB_BINS + 127) / 128, 128, 0, c->stream>>>(c->filter_kind, c->xc, c->theta_ap, sqrt(c->T),
-                                                                  c->qtab);
+smart_status build_filter_table(smart_ctx *c, bool plane, float4 **tab) {
+    if (c->filter_kind == SMART_FILTER_POLY || *tab) return SMART_OK;
+    if (cudaMalloc(tab, QTAB_BINS * sizeof(float4)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(filter table) failed");
+    k_filter_table<<<(QTAB_BINS + 127) / 128, 128, 0, c->stream>>>(c->filter_kind, c->xc, c->theta_ap,
+                                                                  plane ? c->theta_ap : sqrt(c->T), plane ? 1 : 0,
+                                                                  *tab);
     return check_cuda(c, cudaGetLastError(), "k_filter_table");
 }
+
+smart_status ensure_filter_table(smart_ctx *c) { return build_filter_table(c, false, &c->qtab); }
 
 // Toeplitz tables for every ring pair of the pixel-mode table (once per context)
 static smart_status build_toeplitz(smart_ctx *c, const MapArgs &a) {
     const int64_t nring = 4 * (int64_t)c->nside_out - 1;
     const int64_t nidx = nring * a.kmax;
     int32_t *cnt = nullptr, *off = nullptr;
-    if (cudaMalloc(&cnt, (size_t)(2 * nidx + 1) * sizeof(int32_t)) != cudaSuccess) return fail(c, SMART_E_NOMEM, "cudaMalloc(toeplitz counts) failed");
+    if (cudaMallocAsync(&cnt, (size_t)(2 * nidx + 1) * sizeof(int32_t), c->stream) != cudaSuccess)
+        return fail(c, SMART_E_NOMEM, "cudaMallocAsync(toeplitz counts) failed");
     off = cnt + nidx;
     k_toe_count<<<(unsigned)((nidx + 255) / 256), 256, 0, c->stream>>>(a, nring, cnt);
     smart_status st = exclusive_scan_i32(c, cnt, off, nidx, nidx + 1);
     int32_t total = 0;
     if (st == SMART_OK) {
-        cudaMemcpyAsync(&total, off + nidx, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
-        st = check_cuda(c, cudaStreamSynchronize(c->stream), "toeplitz table size");
+        int32_t *h = reinterpret_cast<int32_t *>(c->host_rb);
+        cudaMemcpyAsync(h, off + nidx, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        st = wait_stream(c, "toeplitz table size");
+        total = h[0];
     }
     if (st == SMART_OK && cudaMalloc(&c->toe_info, (size_t)nidx * sizeof(ToeInfo)) != cudaSuccess)
         st = fail(c, SMART_E_NOMEM, "cudaMalloc(toeplitz info) failed");
@@ -363,8 +383,7 @@ static smart_status build_toeplitz(smart_ctx *c, const MapArgs &a) {
         else k_toe_fill<SMART_FILTER_SCHIRMER><<<blocks, 256, 0, c->stream>>>(a, nring, off, c->toe_info, c->toe_geo);
         st = check_cuda(c, cudaGetLastError(), "k_toe_fill");
     }
-    if (st == SMART_OK) st = check_cuda(c, cudaStreamSynchronize(c->stream), "toeplitz build");
-    cudaFree(cnt);
+    cudaFreeAsync(cnt, c->stream);
     return st;
 }
 
@@ -384,10 +403,10 @@ static smart_status build_ring_classes(smart_ctx *c, const MapArgs &a) {
     k_gen_flags<<<blocks, 256, 0, c->stream>>>(c->targets, n, c->nside_out, c->toe_ring, flag);
     st = exclusive_scan_i32(c, flag, idx, n, n);
     if (st != SMART_OK) return st;
-    int32_t last[2] = {0, 0};
+    int32_t *last = reinterpret_cast<int32_t *>(c->host_rb);
     cudaMemcpyAsync(&last[0], idx + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(&last[1], flag + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
-    st = check_cuda(c, cudaStreamSynchronize(c->stream), "general target count");
+    st = wait_stream(c, "general target count");
     if (st != SMART_OK) return st;
     const int64_t ng = (int64_t)last[0] + last[1];
     st = ensure_alloc(c, (void **)&c->gen_list, c->cap_gen_list, ng, sizeof(int32_t), "general target list");
@@ -482,6 +501,37 @@ smart_status prepare_pixel(smart_ctx *c, const smart_maps *out, MapArgs &a) {
     a.toe_ring = c->toe_ring;
     a.gen_list = c->gen_list;
     a.n_gen = a.n > 0 ? c->n_gen : 0;
+    return SMART_OK;
+}
+
+smart_status prepare_tables(smart_ctx *c) {
+    smart_maps none{};
+    MapArgs a{};
+    smart_status st = common_args(c, &none, a);
+    if (st != SMART_OK) return st;
+    // pixel mode: ring pairs and Toeplitz tables (once per context), ring
+    // classes and the general kernel's target list (once per target set)
+    if (!c->rp_pix && (st = build_ring_pairs(c, c->theta_ap, &c->rp_pix, &c->rp_pix_cnt, &c->kmax_pix)) != SMART_OK)
+        return st;
+    a.table = c->rp_pix;
+    a.counts = c->rp_pix_cnt;
+    a.kmax = c->kmax_pix;
+    if (!c->toe_info && (st = build_toeplitz(c, a)) != SMART_OK) return st;
+    a.toe = c->toe_info;
+    a.toe_geo = c->toe_geo;
+    if (a.n > 0 && c->gen_version != c->targets_version && (st = build_ring_classes(c, a)) != SMART_OK) return st;
+    // brute force and projected maps: ring pairs for theta_ap plus the
+    // largest bin-pixel radius (galaxies lie anywhere in their pixel) and
+    // groups of targets
+    if (!c->rp_gal) {
+        const double th = c->theta_ap + max_pixrad(c->nside_bin) * 1.01 + 1e-9;
+        if ((st = build_ring_pairs(c, th, &c->rp_gal, &c->rp_gal_cnt, &c->kmax_gal)) != SMART_OK) return st;
+    }
+    if (c->gal_tiles_version != c->targets_version) {
+        if ((st = build_tiles_log2(c, GAL_GROUP_LOG2, &c->gal_tiles, &c->cap_gal_tiles, &c->n_gal_tiles)) != SMART_OK)
+            return st;
+        c->gal_tiles_version = c->targets_version;
+    }
     return SMART_OK;
 }
 

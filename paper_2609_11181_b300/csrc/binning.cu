@@ -441,23 +441,29 @@ __global__ void k_pixel_sums(const int32_t *__restrict__ off, int64_t npix, cons
     }
 }
 
+// the per-galaxy arrays, grown together (stream-ordered: no host wait)
 static smart_status ensure_gal_buffers(smart_ctx *c, int64_t n) {
     if (n <= c->cap_gal && c->keys) return SMART_OK;
-    cudaStreamSynchronize(c->stream);
     void **bufs[] = {(void **)&c->keys, (void **)&c->keys_alt, (void **)&c->vals, (void **)&c->vals_alt,
                      (void **)&c->rec_geo, (void **)&c->rec_shear, (void **)&c->rec_radec};
     const size_t elem[] = {4, 4, 4, 4, 16, 16, 16};
-    for (void **b : bufs) {
-        if (*b) cudaFree(*b);
-        *b = nullptr;
-    }
-    c->cap_gal = 0;
     const int64_t cap = std::max<int64_t>(n, 1);
-    for (int k = 0; k < 7; ++k)
-        if (cudaMalloc(bufs[k], (size_t)cap * elem[k]) != cudaSuccess)
-            return fail(c, SMART_E_NOMEM, "cudaMalloc(galaxy buffers) failed");
+    for (int k = 0; k < 7; ++k) {
+        int64_t have = *bufs[k] ? c->cap_gal : 0;
+        smart_status st = ensure_alloc(c, bufs[k], have, cap, elem[k], "galaxy buffers");
+        if (st != SMART_OK) {
+            c->cap_gal = 0;
+            return st;
+        }
+    }
     c->cap_gal = cap;
     return SMART_OK;
+}
+
+// a galaxy with invalid coordinates was counted: flag the device status
+// word, which smart_sync reports (the call itself does not wait)
+__global__ void k_flag_invalid(const int *__restrict__ invalid, int *__restrict__ status) {
+    if (*invalid > 0) atomicOr(status, SMART_STATUS_INVALID_COORDS);
 }
 
 static unsigned grid_for(int64_t n, int threads) {
@@ -561,16 +567,8 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     c->have_catalog = true;
     c->n_gal = n;
     c->catalog_version += 1;
-    int inv = 0;
-    cudaMemcpyAsync(&inv, c->d_invalid, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if ((st = check_cuda(c, cudaStreamSynchronize(s), "smart_bin_galaxies")) != SMART_OK) return st;
-    if (inv) {
-        c->have_catalog = false;
-        c->have_binned = false;
-        return fail(c, SMART_E_ARG, "smart_bin_galaxies: " + std::to_string(inv) +
-                                        " galaxies with non-finite ra/dec or |dec| > 90");
-    }
-    return SMART_OK;
+    k_flag_invalid<<<1, 1, 0, s>>>(c->d_invalid, c->d_status);
+    return check_cuda(c, cudaGetLastError(), "smart_bin_galaxies");
 }
 
 __global__ void k_copy_catalog(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,

@@ -21,23 +21,44 @@ smart_status check_cuda(smart_ctx *ctx, cudaError_t e, const char *what) {
     return fail(ctx, e == cudaErrorMemoryAllocation ? SMART_E_NOMEM : SMART_E_CUDA, m);
 }
 
-// grow-only device buffer: reallocates when `need` elements exceed `cap`
+// grow-only device buffer: reallocates when `need` elements exceed `cap`.
+// Stream-ordered (cudaFreeAsync / cudaMallocAsync on the context stream), so
+// that growing a buffer never makes the host wait: the old buffer is freed
+// after the work already queued on the stream, the new one is ready for the
+// work queued after it.
 smart_status ensure_alloc(smart_ctx *ctx, void **p, int64_t &cap, int64_t need, size_t elem, const char *what) {
     if (need <= cap && *p) return SMART_OK;
     if (*p) {
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(*p);
+        if (ctx->async_bufs.erase(*p)) cudaFreeAsync(*p, ctx->stream);
+        else {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(*p);
+        }
         *p = nullptr;
         cap = 0;
     }
     const int64_t n = need > 0 ? need : 1;
-    cudaError_t e = cudaMalloc(p, (size_t)n * elem);
+    cudaError_t e = cudaMallocAsync(p, (size_t)n * elem, ctx->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
-        return fail(ctx, SMART_E_NOMEM, std::string("cudaMalloc(") + what + ") failed");
+        return fail(ctx, SMART_E_NOMEM, std::string("cudaMallocAsync(") + what + ") failed");
     }
+    ctx->async_bufs.insert(*p);
     cap = n;
     return SMART_OK;
+}
+
+smart_status wait_stream(smart_ctx *ctx, const char *what) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) return SMART_OK;
+        if (e != cudaErrorNotReady) return check_cuda(ctx, e, what);
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (ctx->wait_limit_s > 0 && dt > ctx->wait_limit_s)
+            return fail(ctx, SMART_E_TIMEOUT, std::string(what) + ": wait limit passed");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 }  // namespace smart
@@ -72,7 +93,8 @@ extern "C" smart_status smart_create(int nside_out, const smart_filter *filter, 
         cudaMalloc(&c->d_band_count, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_work, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&c->d_work, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->host_rb, 16 * sizeof(int64_t)) != cudaSuccess) {
         if (c->d_fp64_count) cudaFree(c->d_fp64_count);
         delete c;
         return SMART_E_NOMEM;
@@ -90,9 +112,15 @@ extern "C" void smart_destroy(smart_ctx *c) {
                     c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
                     c->toe_ring, c->gen_list, c->gal_tiles, c->raw, c->band, c->d_band_count,
                     c->d_status, c->d_fp64_count, c->bary_off, c->bary_geo, c->bary_sh, c->bary_keys,
-                    c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m, c->avg_buf, c->gen_band, c->d_gen_count};
-    for (void *b : bufs)
-        if (b) cudaFree(b);
+                    c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m, c->avg_buf, c->gen_band, c->d_gen_count,
+                    c->proj_plane, c->proj_xy, c->proj_sh, c->proj_txy, c->qtab_plane, c->annulus_buf};
+    for (void *b : bufs) {
+        if (!b) continue;
+        if (c->async_bufs.count(b)) cudaFreeAsync(b, c->stream);
+        else cudaFree(b);
+    }
+    cudaStreamSynchronize(c->stream);
+    if (c->host_rb) cudaFreeHost(c->host_rb);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -117,6 +145,12 @@ extern "C" smart_status smart_sync(smart_ctx *c, double timeout_s) {
     if (st != SMART_OK) return st;
     if (status) {
         cudaMemset(c->d_status, 0, sizeof(int));
+        if (status & SMART_STATUS_INVALID_COORDS) {
+            int inv = 0;
+            if (c->d_invalid) cudaMemcpy(&inv, c->d_invalid, sizeof(int), cudaMemcpyDeviceToHost);
+            return fail(c, SMART_E_ARG, "smart_bin_galaxies: " + std::to_string(inv) +
+                                            " galaxies with non-finite ra/dec or |dec| > 90 (left out of the catalogue)");
+        }
         if (status & SMART_STATUS_BAND_OVERFLOW)
             return fail(c, SMART_E_OVERFLOW, "guard-band pair list overflowed: map incomplete");
         return fail(c, SMART_E_INTERNAL, "device status " + std::to_string(status));
@@ -144,23 +178,34 @@ extern "C" smart_status smart_set_targets(smart_ctx *c, const int64_t *pix, int6
     st = check_cuda(c, cudaMemcpyAsync(c->targets, pix, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, c->stream),
                     "copy targets");
     if (st != SMART_OK) return st;
-    // validate range and ordering once (a small synchronous check)
+    // validate range and ordering once (read back into pinned memory, a
+    // bounded wait)
     int *bad = nullptr;
     if (cudaMallocAsync(&bad, sizeof(int), c->stream) != cudaSuccess) return fail(c, SMART_E_NOMEM, "flag alloc");
     cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
     const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 148 * 16);
     k_check_targets<<<blocks, 256, 0, c->stream>>>(c->targets, n, npix_of(c->nside_out), bad);
-    int hb = 0;
-    cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    int32_t *hb32 = reinterpret_cast<int32_t *>(c->host_rb);
+    cudaMemcpyAsync(hb32, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaFreeAsync(bad, c->stream);
-    st = check_cuda(c, cudaStreamSynchronize(c->stream), "validate targets");
+    st = wait_stream(c, "smart_set_targets: validate targets");
     if (st != SMART_OK) return st;
+    const int hb = hb32[0];
     if (hb) {
         c->n_targets = 0;
         c->n_tiles = 0;
         return fail(c, SMART_E_ARG, "smart_set_targets: pixels must be unique, ascending and in [0, 12 nside_out^2)");
     }
-    return build_tiles(c);
+    st = build_tiles(c);
+    if (st != SMART_OK) return st;
+    return prepare_tables(c);
+}
+
+extern "C" smart_status smart_set_wait_limit(smart_ctx *c, double seconds) {
+    if (!c) return SMART_E_ARG;
+    if (!(seconds >= 0.0)) return fail(c, SMART_E_ARG, "smart_set_wait_limit: negative limit");
+    c->wait_limit_s = seconds;
+    return SMART_OK;
 }
 
 __global__ void k_pack(const float *__restrict__ G1, const float *__restrict__ G2, const float *__restrict__ W,
@@ -216,10 +261,9 @@ extern "C" smart_status smart_set_binned_packed(smart_ctx *c, const float *px, c
 
 extern "C" int64_t smart_last_fp64_decisions(smart_ctx *c) {
     if (!c) return -1;
-    unsigned long long h = 0;
-    cudaMemcpyAsync(&h, c->d_fp64_count, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
-    return (int64_t)h;
+    cudaMemcpyAsync(c->host_rb + 8, c->d_fp64_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    if (wait_stream(c, "smart_last_fp64_decisions") != SMART_OK) return -1;
+    return c->host_rb[8];
 }
 
 // ------------------------------------------------------------ kernel timing

@@ -158,10 +158,10 @@ smart_status build_ring_pairs(smart_ctx *ctx, double theta_disc, RingPair **out,
     const double Tdisc = (theta_disc == ctx->theta_ap) ? ctx->T : 4.0 * sin(0.5 * theta_disc) * sin(0.5 * theta_disc);
     k_ring_pairs<<<(unsigned)((nring + 127) / 128), 128, 0, ctx->stream>>>(N0, N1, theta_disc, Tdisc, k, t, c, ov);
     smart_status st = check_cuda(ctx, cudaGetLastError(), "k_ring_pairs launch");
-    int hov = 0;
-    if (st == SMART_OK) st = check_cuda(ctx, cudaMemcpyAsync(&hov, ov, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "ring-pair overflow flag");
-    if (st == SMART_OK) st = check_cuda(ctx, cudaStreamSynchronize(ctx->stream), "ring-pair build");
-    if (st == SMART_OK && hov) st = fail(ctx, SMART_E_INTERNAL, "ring-pair table row overflow");
+    int32_t *hov = reinterpret_cast<int32_t *>(ctx->host_rb);
+    if (st == SMART_OK) st = check_cuda(ctx, cudaMemcpyAsync(hov, ov, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "ring-pair overflow flag");
+    if (st == SMART_OK) st = wait_stream(ctx, "ring-pair build");
+    if (st == SMART_OK && hov[0]) st = fail(ctx, SMART_E_INTERNAL, "ring-pair table row overflow");
     if (st != SMART_OK) {
         cudaFree(t);
         cudaFree(c);

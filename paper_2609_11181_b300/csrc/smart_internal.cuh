@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_set>
 #include <utility>
 #include <vector>
 
@@ -266,7 +267,7 @@ static_assert(sizeof(RingPair) == 64, "RingPair layout");
 enum { RP_SHIFTED = 1, RP_WIDE = 2, RP_WHOLE = 4 };
 
 // bits of the device status word read back by smart_sync
-enum { SMART_STATUS_BAND_OVERFLOW = 1 };
+enum { SMART_STATUS_BAND_OVERFLOW = 1, SMART_STATUS_INVALID_COORDS = 2 };
 
 // Per ring pair of the pixel-mode table: where its per-offset geometry sits
 // in the Toeplitz pool (off = -1: not a Toeplitz pair), the candidate
@@ -290,6 +291,9 @@ struct smart_ctx {
     double area = 0;           // 2 pi (1 - cos theta_ap)
     cudaStream_t stream = nullptr;
     std::string err;
+    double wait_limit_s = 600.0;     // deadline of the waits inside set-up calls
+    int64_t *host_rb = nullptr;      // pinned host slots for the set-up calls' read-backs (16)
+    std::unordered_set<void *> async_bufs;   // buffers from the stream-ordered allocator
 
     // targets
     int64_t *targets = nullptr;
@@ -376,6 +380,17 @@ struct smart_ctx {
     int64_t cap_gen_count = 0;
     int64_t band_slot_limit = 0;                     // > 0: cap on those slots (testing aid)
 
+    // Cartesian (projected) estimator (Sect. 2.2, Sect. 5.2.1): the plane of
+    // the last projection, plane records of the sorted galaxies and targets
+    double *proj_plane = nullptr;                    // 9 doubles: c, e_c, n_c
+    float4 *proj_xy = nullptr, *proj_sh = nullptr;   // per galaxy: (x hi, y hi, x lo, y lo), rotated shear
+    int64_t cap_proj = 0, cap_proj_sh = 0;
+    float4 *proj_txy = nullptr;                      // per target: (x hi, y hi, x lo, y lo); NaN: no image
+    int64_t cap_proj_t = 0;
+    float4 *qtab_plane = nullptr;                    // filter table on the plane distance (tabulated filters)
+    double *annulus_buf = nullptr;                   // annulus sums
+    int64_t cap_annulus = 0;
+
     // diagnostics
     unsigned long long *d_fp64_count = nullptr;
     bool timing = false;                             // record events around each kernel launch
@@ -389,6 +404,9 @@ namespace smart {
 smart_status fail(smart_ctx *ctx, smart_status st, const std::string &msg);
 smart_status check_cuda(smart_ctx *ctx, cudaError_t e, const char *what);
 smart_status ensure_alloc(smart_ctx *ctx, void **p, int64_t &cap, int64_t need, size_t elem, const char *what);
+// wait for the context stream, polling, at most ctx->wait_limit_s seconds
+// (SMART_E_TIMEOUT after that); used by the set-up calls only
+smart_status wait_stream(smart_ctx *ctx, const char *what);
 
 // geometry.cu
 smart_status build_ring_pairs(smart_ctx *ctx, double theta_disc, RingPair **out, int **cnt, int *kmax);
@@ -403,7 +421,14 @@ smart_status build_tiles(smart_ctx *ctx);
 struct MapArgs;
 smart_status prepare_pixel(smart_ctx *c, const smart_maps *out, MapArgs &a);
 smart_status launch_count_prefix(smart_ctx *c);
+// filter table on the chord (spherical maps) or on the plane distance
+// (projected map) of the tabulated filters; no-op for the polynomial filter
+smart_status build_filter_table(smart_ctx *c, bool plane, float4 **tab);
 smart_status build_tiles_log2(smart_ctx *ctx, int log2_slots, int64_t **tiles, int64_t *cap, int64_t *n_tiles);
+// every table the maps need for the current targets (pixel mode and brute
+// force), built in smart_set_targets so that the map calls never wait
+smart_status prepare_tables(smart_ctx *c);
+constexpr int GAL_GROUP_LOG2 = 2;    // brute force and projected: groups of 4 targets per warp
 
 // context.cu
 smart_status ensure_own_binned_map(smart_ctx *ctx);

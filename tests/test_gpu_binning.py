@@ -98,12 +98,20 @@ def test_empty_catalog(cuda_device):
 
 
 def test_invalid_coordinates_rejected(cuda_device):
+    # the call does not wait; the device counts the two invalid galaxies, the
+    # next sync reports them (SMART_E_ARG), and they are left out of the
+    # catalogue; the sync after that is clean
     ctx = api.Context(16, 30.0, nside_bin=16)
     ra = torch.tensor([10.0, float("nan"), 20.0], dtype=torch.float64, device=cuda_device)
     dec = torch.tensor([0.0, 0.0, 95.0], dtype=torch.float64, device=cuda_device)
     e = torch.zeros(3, dtype=torch.float32, device=cuda_device)
-    with pytest.raises(SmartError, match="2 galaxies"):
-        ctx.bin_galaxies(ra, dec, e, e, None)
+    ctx.bin_galaxies(ra, dec, e, e, None)
+    with pytest.raises(SmartError, match="2 galaxies") as err:
+        ctx.sync(60)
+    assert "SMART_E_ARG" in str(err.value)
+    perm, pix, off = ctx.get_catalog(3)
+    ctx.sync(60)
+    assert int(off[-1]) == 1 and int(perm[0]) == 0
 
 
 @pytest.mark.parametrize("nside", [1, 16, 256, 4096, 8192])

@@ -79,3 +79,37 @@ def test_sync_deadline_times_out_and_context_stays_usable(cuda_device):
     ctx.sync(60)
     for k in ref:
         assert torch.equal(out[k], ref[k]), k
+
+
+def test_map_calls_return_before_the_work_completes(cuda_device):
+    """The boundary's map calls only enqueue work: with the context stream
+    held by a long probe kernel, smart_bin_galaxies and every map call return
+    at once (the stream is still busy afterwards), smart_sync then waits, and
+    the maps equal those of a quiet stream."""
+    import time
+    cat = catalog(23, 80_000, 200.0, 35.0, 4.0, w_range=(0.5, 1.5))
+    tg = torch.from_numpy(cap_targets(256, 200.0, 35.0, 3.0)).to(cuda_device)
+    c = cat.to(cuda_device)
+
+    def run(busy):
+        ctx = api.Context(256, 20.0, "schirmer", nside_bin=512)
+        ctx.set_targets(tg)                 # set-up: builds the tables (may wait)
+        if busy:
+            api.fma_probe(32, 1 << 16, 8)   # about 0.7 s of FMA work on the same stream
+        t0 = time.perf_counter()
+        ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+        outs = [ctx.map_bruteforce(), ctx.map_pixel(), ctx.map_barycentre(), ctx.map_projected(200.0, 35.0)]
+        dt = time.perf_counter() - t0
+        pending = not torch.cuda.current_stream().query()
+        ctx.sync(120)
+        res = [{k: v.clone() for k, v in o.items()} for o in outs]
+        ctx.close()
+        return dt, pending, res
+
+    dt, pending, busy_maps = run(True)
+    assert pending, "the stream was idle right after the calls: some call waited"
+    assert dt < 0.25, f"the calls took {dt:.3f} s on a busy stream"
+    _, _, quiet_maps = run(False)
+    for a, b in zip(busy_maps, quiet_maps):
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
