@@ -31,7 +31,7 @@ struct BatchItem {
 
 // the Toeplitz tiles of every map, claimed longest first by resident CTAs
 template <int KIND>
-__global__ void __launch_bounds__(NT, 8) k_pixel_batched(const MapArgs *__restrict__ maps,
+__global__ void __launch_bounds__(NT, TOE_CTAS_PER_SM) k_pixel_batched(const MapArgs *__restrict__ maps,
                                                           const BatchItem *__restrict__ items, int64_t n_items,
                                                           int *__restrict__ work) {
     __shared__ __align__(16) ToeShared S;

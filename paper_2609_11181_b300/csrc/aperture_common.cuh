@@ -80,10 +80,18 @@ __device__ __forceinline__ float sep2_from_chord2(float s2) {
     return s2 * fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 3150.0f, 1.0f / 560.0f), 1.0f / 90.0f), 1.0f / 12.0f), 1.0f);
 }
 
+// square root to within a couple of ulps (the hardware approximation; exact
+// for 0): a table coordinate, not a result
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Q from the cubic table, indexed by the chord s = sqrt(s2) (uniform bins of
 // s / s_ap; Q is smooth in s because the separation d(s) is)
 __device__ __forceinline__ float qtab_eval(const float4 *tab, float s2, float scale) {
-    const float f = s2 * rsqrtf(fmaxf(s2, 1e-30f)) * scale;
+    const float f = sqrt_approx(s2) * scale;
     const int i = min((int)f, QTAB_BINS - 1);
     const float t = f - (float)i;
     const float4 c = tab[i];

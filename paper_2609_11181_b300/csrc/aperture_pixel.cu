@@ -147,7 +147,7 @@ __global__ void k_toe_fill(const MapArgs a, int64_t nring, const int32_t *__rest
 // output rings are skipped (the general kernel has them).
 // ------------------------------------------------------------------------
 template <int KIND>
-__global__ void __launch_bounds__(NT, 8) k_pixel_toeplitz(const MapArgs a) {
+__global__ void __launch_bounds__(NT, TOE_CTAS_PER_SM) k_pixel_toeplitz(const MapArgs a) {
     __shared__ __align__(16) ToeShared S;
     __shared__ int s_tile;
     for (;;) {
@@ -567,7 +567,7 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     const bool averaged = c->norm == SMART_NORM_AVERAGED;
     if (averaged && (st = averaged_pixel_input(c, a.PX, &a.PX)) != SMART_OK) return st;
     if (a.n_gen < a.n) {
-        const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * 8);
+        const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * TOE_CTAS_PER_SM);
         KernelTimer timer(c, SMART_KT_PIXEL_TOEPLITZ);
         if (c->filter_kind == SMART_FILTER_POLY) k_pixel_toeplitz<SMART_FILTER_POLY><<<grid, NT, 0, c->stream>>>(a);
         else k_pixel_toeplitz<SMART_FILTER_SCHIRMER><<<grid, NT, 0, c->stream>>>(a);

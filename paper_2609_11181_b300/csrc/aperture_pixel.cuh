@@ -25,22 +25,22 @@
 namespace smart {
 
 
-constexpr int TS = 256;           // azimuth slots per tile (aligned blocks of a ring)
-constexpr int TS_LOG2 = 8;
+constexpr int TS = 512;           // azimuth slots per tile (aligned blocks of a ring)
+constexpr int TS_LOG2 = 9;
 constexpr int NT = 64;            // threads per CTA
-constexpr int RB = 4;             // consecutive slots per thread
+constexpr int RB = 8;             // consecutive slots per thread
 constexpr int NCAND = 120;        // longest Toeplitz candidate run kept in shared memory
 constexpr int SEGN = TS + NCAND + 8;
-static_assert(SEGN % 32 == 0, "staging layout works on blocks of 32");
-
+static_assert(SEGN % 8 == 0, "staging layout works on rows of 8 pixels");
 static_assert(TS == NT * RB, "tile = threads x slots per thread");
+constexpr int TOE_CTAS_PER_SM = 6;  // resident CTAs of the Toeplitz kernels (registers and shared memory)
 
-// shared-memory position of staged pixel m: 4 x 8 transposition inside each
-// block of 32, so that lanes reading m = 4 l + c hit 8 distinct 16-byte
-// bank groups in every quarter warp
-__device__ __forceinline__ int tpos(int m) { return (m & ~31) | ((m & 3) << 3) | ((m >> 2) & 7); }
-__device__ __forceinline__ int tpos_inv(int q) { return (q & ~31) | ((q & 7) << 2) | ((q >> 3) & 3); }
-__device__ __forceinline__ int qbase(int Q) { return Q + 3 * (Q & ~7); }   // tpos(4Q)
+// shared-memory position of staged pixel m: rows of eight 16-byte pixels
+// (128 bytes, every bank once), the pixel's slot within its row XOR-ed with
+// the row index.  Thread t reads pixels m = 8 t + d: the eight threads of a
+// quarter warp then sit in eight consecutive rows, and the XOR puts their
+// pixels in eight different 16-byte bank groups for every d.
+__device__ __forceinline__ int tpos(int m) { return (m & ~7) | ((m ^ (m >> 3)) & 7); }
 
 // the float64 membership decision for a pair inside the guard band
 static __device__ __noinline__ bool exact_member_pix(int64_t N0, int64_t N1, double T, unsigned long long *counter,
@@ -124,6 +124,46 @@ __device__ __forceinline__ int wrap_start(const RingPair &R, int Xi, int k) {
     return kk;
 }
 
+// The certain members of one ring pair that do not cross the bin ring's
+// seam: bin pixels pbeg .. pbeg + cnt - 1 at lattice offsets kf, kf + 1, ...
+// No test, no select: every pair is a member.  The bin pixel's data is loaded
+// one iteration ahead (the last load repeats, never past the run).
+template <int KIND, int MODE>
+__device__ __forceinline__ void certain_run(const MapArgs &a, const RingPair &R, const float4 *qtab, float u0,
+                                            float kf, int pbeg, int cnt, float &pe, float &pb, float &pv,
+                                            float &pw) {
+    const float4 *pp = a.PX + pbeg;
+    float4 gn = __ldg(pp);
+#pragma unroll 2
+    for (int i = 0; i < cnt; ++i) {
+        const float4 g = gn;
+        gn = __ldg(pp + min(i + 1, cnt - 1));
+        // u from the offset each time (not by repeated addition): the
+        // target's own pixel must get u = 0 exactly, so that it carries no
+        // shear
+        const float u = fmaf(kf, R.dphi, u0);
+        kf += 1.0f;
+        float sinu, h;
+        sin_hav<MODE>(u, sinu, h);
+        const float s2 = fmaf(R.B, h, R.A);
+        const float x = R.mrho0 * sinu;
+        const float y = fmaf(R.D, h, R.C);
+        const float xx = x * x;
+        const float sd2 = fmaf(y, y, xx);
+        const float cc = fmaf(y, y, -xx);
+        const float ss = -2.0f * x * y;
+        const float Q = filter_Q<KIND>(a.f, qtab, s2);
+        // sd2 = 0 only at the target's own centre, where cc = ss = 0
+        // exactly; elsewhere sd2 is at least a squared bin spacing, far
+        // above the offset, which only keeps w finite there
+        const float w = __fdividef(Q, sd2 + 1e-30f);
+        pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
+        pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
+        pv = fmaf(Q * Q, g.z, pv);
+        pw += g.w;
+    }
+}
+
 // pixel-mode general pair loop for one target and one ring pair; MODE picks
 // the sine series by the largest |u| of the ring pair (0: <= 0.05 rad,
 // 1: <= 0.45 rad, 2: |u| <= pi).  Offsets within hw_in are members for
@@ -131,7 +171,9 @@ __device__ __forceinline__ int wrap_start(const RingPair &R, int Xi, int k) {
 // the count prefix.  The few offsets between hw_in and the window's edges
 // are tested; those inside the float32 guard band are only counted
 // (nband_out): they are decided in float64 once the target's other pairs
-// are summed.
+// are summed.  A window that stays inside the bin ring's pixel range (all
+// but the targets next to the seam at azimuth 0) takes one run with no
+// wrapping arithmetic.
 template <int KIND, int MODE>
 __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
                                                 const LatticeDiv &ld, const float4 *qtab, float &pe, float &pb,
@@ -149,9 +191,17 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
         ih = kh;
     }
     const float u0 = fr * R.dphi;
-    // certain members: bin pixels [kk0, nr) then [0, ...) when they wrap
     const int len = ih - il + 1;
-    if (len > 0) {
+    const bool inside = Xi + kl >= 0 && Xi + kh < R.nr;
+    if (inside) {
+        if (len > 0) {
+            const int pbeg = R.start + Xi + il;
+            certain_run<KIND, MODE>(a, R, qtab, u0, (float)il, pbeg, len, pe, pb, pv, pw);
+            nn += __ldg(a.NPRE + pbeg + len) - __ldg(a.NPRE + pbeg);
+            nm += len;
+        }
+    } else if (len > 0) {
+        // certain members: bin pixels [kk0, nr) then [0, ...) when they wrap
         const int kk0 = wrap_start(R, Xi, il);
         const int n1 = min(len, R.nr - kk0);
 #pragma unroll 1
@@ -159,37 +209,8 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             const int cnt = part == 0 ? n1 : len - n1;
             if (cnt <= 0) continue;
             const int pbeg = part == 0 ? R.start + kk0 : R.start;
-            const int plast = pbeg + cnt - 1;
-            float kf = (float)(part == 0 ? il : il + n1);
-            // the bin pixel's data is loaded one iteration ahead (the load of
-            // the last pixel is repeated, never past the run)
-            float4 gn = __ldg(a.PX + pbeg);
-#pragma unroll 2
-            for (int i = 0; i < cnt; ++i) {
-                const float4 g = gn;
-                gn = __ldg(a.PX + min(pbeg + i + 1, plast));
-                const float u = fmaf(kf, R.dphi, u0);
-                kf += 1.0f;
-                float sinu, h;
-                sin_hav<MODE>(u, sinu, h);
-                const float s2 = fmaf(R.B, h, R.A);
-                const float x = R.mrho0 * sinu;
-                const float y = fmaf(R.D, h, R.C);
-                const float xx = x * x;
-                const float sd2 = fmaf(y, y, xx);
-                const float cc = fmaf(y, y, -xx);
-                const float ss = -2.0f * x * y;
-                const float Q = filter_Q<KIND>(a.f, qtab, s2);
-                // sd2 = 0 only at the target's own centre, where cc = ss = 0
-                // exactly; elsewhere sd2 is at least a squared bin spacing, far
-                // above the offset, which only keeps w finite there
-                const float w = __fdividef(Q, sd2 + 1e-30f);
-                pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
-                pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
-                pv = fmaf(Q * Q, g.z, pv);
-                pw += g.w;
-            }
-            nn += __ldg(a.NPRE + plast + 1) - __ldg(a.NPRE + pbeg);
+            certain_run<KIND, MODE>(a, R, qtab, u0, (float)(part == 0 ? il : il + n1), pbeg, cnt, pe, pb, pv, pw);
+            nn += __ldg(a.NPRE + pbeg + cnt) - __ldg(a.NPRE + pbeg);
             nm += cnt;
         }
     }
@@ -203,7 +224,9 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             float sinu, h;
             sin_hav<MODE>(u, sinu, h);
             const float s2 = fmaf(R.B, h, R.A);
-            if (s2 < a.Tlo) pixel_pair<KIND, MODE>(a, R, qtab, u, R.start + wrap_start(R, Xi, k), pe, pb, pv, pw, nn, nm);
+            if (s2 < a.Tlo)
+                pixel_pair<KIND, MODE>(a, R, qtab, u, R.start + (inside ? Xi + k : wrap_start(R, Xi, k)), pe, pb, pv,
+                                       pw, nn, nm);
             else nband += s2 <= a.Thi ? 1 : 0;
         }
     }
@@ -259,12 +282,17 @@ __device__ __forceinline__ int ring_range_count(const int32_t *pre, int start, i
 // ------------------------------------------------------------------------
 // Toeplitz kernel: output rings whose every ring pair is a Toeplitz pair.
 // Persistent CTAs take tiles of up to TS slots of one ring; thread tid owns
-// the slots 4 tid .. 4 tid + 3 and slides a window of staged pixels over
-// them.  Per ring pair the CTA stages, with cp.async into a double buffer,
-// the bin-ring segment the tile needs (16-byte pixels in the transposed
-// layout), the per-offset geometry of the ring pair and the prefix counts
-// of the segment; ring pair e + 1 is in flight while e is summed.  Tiles
-// of other rings are skipped (the general kernel has them).
+// the RB = 8 slots 8 tid .. 8 tid + 7 and keeps the eight bin pixels its
+// slots need at the current offset in registers: register W[p & 7] holds bin
+// pixel p, so at offset dd slot r reads W[(dd + r) & 7], and each step loads
+// one new pixel (8 tid + dd + 7) and one geometry entry for eight pairs.
+// Steps are unrolled by eight so that the register of every pixel is fixed
+// at compile time (no moves).  Per ring pair the CTA stages, with cp.async
+// into a double buffer, the bin-ring segment the tile needs (16-byte pixels
+// in the XOR-swizzled row layout of tpos), the per-offset geometry and the
+// prefix counts of the segment (eight planes, conflict-free for the stride-8
+// slots); ring pair e + 1 is in flight while e is summed.  Tiles of other
+// rings are skipped (the general kernel has them).
 // ------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -281,10 +309,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ int wraps(int a, int b) { return a < 0 ? -1 : (a >= b ? 1 : 0); }
 
 constexpr int PREN = SEGN + 8;
-constexpr int PREQ = PREN / 4;        // prefix counts in 4 planes: m -> (m & 3) * PREQ + (m >> 2)
-static_assert(PREN % 4 == 0, "prefix planes");
+constexpr int PSTR = PREN / 8;        // prefix counts in 8 planes: m -> (m & 7) * PSTR + (m >> 3); a warp
+                                      // reads one plane at consecutive positions
+static_assert(PREN % 8 == 0, "prefix planes");
 
-__device__ __forceinline__ int ppos(int m) { return (m & 3) * PREQ + (m >> 2); }
+__device__ __forceinline__ int ppos(int m) { return (m & 7) * PSTR + (m >> 3); }
 
 // what a tile needs of one of its ring pairs; the tile's first TPN ring
 // pairs are read into shared memory once, at the start of the tile
@@ -316,19 +345,16 @@ __device__ __forceinline__ ToeStage tile_param(const MapArgs &a, const ToeStage 
 
 // issue the copies of ring pair e of a tile into buffer b
 __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par, int64_t row0, int e, int jbase,
-                                          int nslots, float4 (*seg)[SEGN], float4 (*geo)[NCAND], int (*pre)[PREN],
+                                          int nslots, float4 (*seg)[SEGN], float4 (*geo)[NCAND], int (*pre)[8 * PSTR],
                                           int b, int tid) {
     const ToeStage t = tile_param(a, par, row0, e, jbase);
     if (t.L > 0) {
-        const int nseg = min(SEGN, nslots + t.L + 3);
-        const int nseg32 = (nseg + 31) & ~31;
+        const int nseg = min(SEGN, nslots + t.L + 7);
         // -nr < k0 + m < 2 nr for every staged m (the window is shorter than the ring)
-        for (int q = tid; q < nseg32; q += NT) {        // shared-memory positions in order
-            const int m = tpos_inv(q);
-            if (m >= nseg) continue;
+        for (int m = tid; m < nseg; m += NT) {
             int kk = t.k0 + m;
             kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
-            cp_async16(&seg[b][q], a.PX + t.start + kk);
+            cp_async16(&seg[b][tpos(m)], a.PX + t.start + kk);
         }
         for (int c = tid; c < t.L; c += NT) cp_async16(&geo[b][c], a.toe_geo + t.off + t.da + c);
         const int npre = min(PREN, nslots + t.L + 1);
@@ -344,13 +370,38 @@ __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par,
 struct ToeShared {
     float4 seg[2][SEGN];
     float4 geo[2][NCAND];
-    int pre[2][PREN];
+    int pre[2][8 * PSTR];
     int slot_t[TS];
     ToeStage par[TPN];
 };
 
+// the pair contribution of slot r: geometry G (Q cos 2psi, Q sin 2psi,
+// -Q sin 2psi, Q^2) on pixel P (G1, G2, S2, W)
+#define SMART_ACC(r, P, G)                               \
+    pe[r] = fmaf(G.x, P.x, fmaf(G.y, P.y, pe[r]));     \
+    pb[r] = fmaf(G.x, P.y, fmaf(G.z, P.x, pb[r]));     \
+    pv[r] = fmaf(G.w, P.z, pv[r]);                     \
+    pw[r] += P.w;
+
+// one offset step j of an eight-step block starting at offset dd0 (a
+// multiple of 8): load pixel 8 tid + dd0 + j + 7 into W[(j + 7) & 7] (its
+// row is rowA for j = 0 and rowA + 1 otherwise), then the eight pairs
+#define SMART_TOE_STEP(j)                                                                   \
+    {                                                                                      \
+        constexpr int cj = ((j) + 7) & 7;                                                  \
+        const int row = (j) == 0 ? rowA : rowA + 1;                                        \
+        W[cj] = sg[(row << 3) | (cj ^ (row & 7))];                                         \
+        const float4 G = gb[(j)];                                                          \
+        SMART_ACC(0, W[(j) & 7], G) SMART_ACC(1, W[((j) + 1) & 7], G)                      \
+        SMART_ACC(2, W[((j) + 2) & 7], G) SMART_ACC(3, W[((j) + 3) & 7], G)                \
+        SMART_ACC(4, W[((j) + 4) & 7], G) SMART_ACC(5, W[((j) + 5) & 7], G)                \
+        SMART_ACC(6, W[((j) + 6) & 7], G) SMART_ACC(7, W[((j) + 7) & 7], G)                \
+    }
+
 // one tile of a Toeplitz output ring, summed by the whole CTA (NT threads);
-// ends with a barrier, so the shared buffers are free on return
+// ends with a barrier, so the shared buffers are free on return.  Sums are
+// compensated (Kahan) every second ring pair: the float32 partial sums of
+// two ring pairs (a few dozen terms) enter the compensated totals together.
 template <int KIND>
 __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, ToeShared &S) {
     auto &seg = S.seg;
@@ -374,19 +425,17 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
     toe_stage(a, S.par, row0, 0, jbase, nslots, seg, geo, pre, 0, tid);
 
     const int s0 = RB * tid;
-    int tix[RB];
     bool any = false;
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-        tix[r] = (s0 + r < nslots) ? slot_t[s0 + r] : -1;
-        any |= tix[r] >= 0;
-    }
+    for (int r = 0; r < RB; ++r) any |= (s0 + r < nslots) && slot_t[s0 + r] >= 0;
     float SE[RB], cSE[RB], SB[RB], cSB[RB], SV[RB], SW[RB], cSW[RB];
     int NN[RB], NM[RB];
+    float pe[RB], pb[RB], pv[RB], pw[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         SE[r] = cSE[r] = SB[r] = cSB[r] = SV[r] = SW[r] = cSW[r] = 0.f;
         NN[r] = NM[r] = 0;
+        pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
     }
 
     for (int e = 0; e < nent; ++e) {
@@ -397,89 +446,92 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
         const ToeStage cur = tile_param(a, S.par, row0, e, jbase);
         const int L = cur.L;
         if (L > 0 && any) {
-            float pe[RB], pb[RB], pv[RB], pw[RB];
-#pragma unroll
-            for (int r = 0; r < RB; ++r) pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
-            const float4 *g = geo[b];
             const float4 *sg = seg[b];
-            // slot s0 + r uses staged pixel s0 + r + dd for dd in [0, L)
-            float4 P0 = sg[tpos(s0)], P1 = sg[tpos(s0 + 1)], P2 = sg[tpos(s0 + 2)];
-            const int L4 = L & ~3;
-#define SMART_ACC(r, P, G)                        \
-pe[r] = fmaf(G.x, P.x, fmaf(G.y, P.y, pe[r])); \
-pb[r] = fmaf(G.x, P.y, fmaf(G.z, P.x, pb[r])); \
-pv[r] = fmaf(G.w, P.z, pv[r]);                 \
-pw[r] += P.w;
-            for (int dd = 0; dd < L4; dd += 4) {
-                // pixels s0 + dd + 3 .. s0 + dd + 6: quad tid + dd/4 (lane 3), quad + 1 (lanes 0..2)
-                const int Q = tid + (dd >> 2);
-                const int b0 = qbase(Q), b1 = qbase(Q + 1);
-                {
-                    const float4 P3 = sg[b0 + 24];
-                    const float4 G = g[dd];
-                    SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
-                    P0 = P3;
-                }
-                {
-                    const float4 P4 = sg[b1];
-                    const float4 G = g[dd + 1];
-                    SMART_ACC(0, P1, G) SMART_ACC(1, P2, G) SMART_ACC(2, P0, G) SMART_ACC(3, P4, G)
-                    P1 = P4;
-                }
-                {
-                    const float4 P5 = sg[b1 + 8];
-                    const float4 G = g[dd + 2];
-                    SMART_ACC(0, P2, G) SMART_ACC(1, P0, G) SMART_ACC(2, P1, G) SMART_ACC(3, P5, G)
-                    P2 = P5;
-                }
-                {
-                    const float4 P6 = sg[b1 + 16];
-                    const float4 G = g[dd + 3];
-                    SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P6, G)
-                    // window for the next block: pixels s0 + dd + 4, + 5, + 6
-                    P0 = P1;
-                    P1 = P2;
-                    P2 = P6;
+            float4 W[8];
+            // pixels 8 tid .. 8 tid + 6 (row tid); the steps load the rest
+#pragma unroll
+            for (int c = 0; c < 7; ++c) W[c] = sg[(tid << 3) | (c ^ (tid & 7))];
+            int dd0 = 0;
+            for (; dd0 + 8 <= L; dd0 += 8) {
+                const int rowA = tid + (dd0 >> 3);
+                const float4 *gb = geo[b] + dd0;
+                SMART_TOE_STEP(0) SMART_TOE_STEP(1) SMART_TOE_STEP(2) SMART_TOE_STEP(3)
+                SMART_TOE_STEP(4) SMART_TOE_STEP(5) SMART_TOE_STEP(6) SMART_TOE_STEP(7)
+            }
+            const int rem = L - dd0;
+            if (rem > 0) {
+                const int rowA = tid + (dd0 >> 3);
+                const float4 *gb = geo[b] + dd0;
+                SMART_TOE_STEP(0)
+                if (rem > 1) {
+                    SMART_TOE_STEP(1)
+                    if (rem > 2) {
+                        SMART_TOE_STEP(2)
+                        if (rem > 3) {
+                            SMART_TOE_STEP(3)
+                            if (rem > 4) {
+                                SMART_TOE_STEP(4)
+                                if (rem > 5) {
+                                    SMART_TOE_STEP(5)
+                                    if (rem > 6) SMART_TOE_STEP(6)
+                                }
+                            }
+                        }
+                    }
                 }
             }
-            for (int dd = L4; dd < L; ++dd) {
-                const float4 P3 = sg[tpos(s0 + dd + 3)];
-                const float4 G = g[dd];
-                SMART_ACC(0, P0, G) SMART_ACC(1, P1, G) SMART_ACC(2, P2, G) SMART_ACC(3, P3, G)
-                P0 = P1;
-                P1 = P2;
-                P2 = P3;
-            }
-#undef SMART_ACC
             // galaxies in [k0 + s, k0 + s + L) from the staged prefix, with the
             // ring total added for every pass over the ring's end
-            const int ring_tot = cur.tot;
+            const int *pr = pre[b];
+            const bool seam = cur.k0 + s0 < 0 || cur.k0 + s0 + RB - 1 + L >= cur.nr;
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
-                if (tix[r] < 0) continue;
+                int n = pr[ppos(s0 + r + L)] - pr[ppos(s0 + r)];
+                if (seam) {
+                    const int lo = cur.k0 + s0 + r;
+                    n += (wraps(lo + L, cur.nr) - wraps(lo, cur.nr)) * cur.tot;
+                }
+                NN[r] += n;
+                NM[r] += L;
+            }
+            if ((e & 1) || e + 1 == nent) {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    kahan_add(SE[r], cSE[r], pe[r]);
+                    kahan_add(SB[r], cSB[r], pb[r]);
+                    SV[r] += pv[r];
+                    kahan_add(SW[r], cSW[r], pw[r]);
+                    pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
+                }
+            }
+        } else if (any && ((e & 1) || e + 1 == nent)) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
                 kahan_add(SE[r], cSE[r], pe[r]);
                 kahan_add(SB[r], cSB[r], pb[r]);
                 SV[r] += pv[r];
                 kahan_add(SW[r], cSW[r], pw[r]);
-                NM[r] += L;
-                const int lo = cur.k0 + s0 + r;
-                NN[r] += pre[b][ppos(s0 + r + L)] - pre[b][ppos(s0 + r)] +
-                         (wraps(lo + L, cur.nr) - wraps(lo, cur.nr)) * ring_tot;
+                pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
             }
         }
-        // ---- guard-band offsets: decided per target in float64
-        if (any && cur.namb > 0) {
+    }
+    // ---- guard-band offsets, after every ring pair (the hot loop's
+    // registers are dead here): decided per target in float64
+    if (any) {
+        for (int e = 0; e < nent; ++e) {
             const ToeInfo ti = a.toe[row0 + e];
+            if (ti.namb <= 0) continue;
+            const int nr = __ldg(&a.table[row0 + e].nr), start = __ldg(&a.table[row0 + e].start);
             for (int ia = 0; ia < ti.namb; ++ia) {
                 const int c = ia == 0 ? ti.amb0 : (ia == 1 ? ti.amb1 : ti.amb2);
                 const float4 G = __ldg(a.toe_geo + ti.off + c);
 #pragma unroll
                 for (int r = 0; r < RB; ++r) {
-                    if (tix[r] < 0) continue;
+                    if (s0 + r >= nslots || slot_t[s0 + r] < 0) continue;
                     const int64_t pix = ring_start0 + jbase + s0 + r;
-                    int kk = (jbase + s0 + r + ti.dlo + c) % cur.nr;
-                    if (kk < 0) kk += cur.nr;
-                    const int p = cur.start + kk;
+                    int kk = (jbase + s0 + r + ti.dlo + c) % nr;
+                    if (kk < 0) kk += nr;
+                    const int p = start + kk;
                     if (!exact_member(a, pix, p)) continue;
                     const float4 px = __ldg(a.PX + p);
                     kahan_add(SE[r], cSE[r], fmaf(G.x, px.x, G.y * px.y));
@@ -494,11 +546,14 @@ pw[r] += P.w;
     }
     cp_async_wait_all();
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
-        if (tix[r] >= 0)
-            finalise(a, tb + tix[r], SE[r], cSE[r], SB[r], cSB[r], SV[r], 0.f, SW[r], cSW[r], NN[r], NM[r]);
+    for (int r = 0; r < RB; ++r) {
+        const int ti = (s0 + r < nslots) ? slot_t[s0 + r] : -1;
+        if (ti >= 0) finalise(a, tb + ti, SE[r], cSE[r], SB[r], cSB[r], SV[r], 0.f, SW[r], cSW[r], NN[r], NM[r]);
+    }
     __syncthreads();   // slot map and buffers are rewritten by the next tile
 }
+#undef SMART_TOE_STEP
+#undef SMART_ACC
 
 // is this tile on an output ring of the Toeplitz kernel?
 __device__ __forceinline__ bool toeplitz_tile_wanted(const MapArgs &a, int64_t tile) {

@@ -247,7 +247,7 @@ __device__ __forceinline__ bool member64(double x0, double y0, double z0,
 // with u the azimuth difference and (x, y) the direction from the point to
 // the centre in the point's (East, North) tangent basis.
 // ---------------------------------------------------------------------------
-struct RingPair {
+struct __align__(16) RingPair {
     int start;      // first pixel of the bin ring
     int nr;         // pixels in the bin ring
     int flags;      // bit0: shifted bin ring, bit1: wide (slow trig), bit2: whole ring
