@@ -25,15 +25,15 @@
 namespace smart {
 
 
-constexpr int TS = 512;           // azimuth slots per tile (aligned blocks of a ring)
-constexpr int TS_LOG2 = 9;
-constexpr int NT = 64;            // threads per CTA
+constexpr int TS = 256;           // azimuth slots per tile (aligned blocks of a ring)
+constexpr int TS_LOG2 = 8;
+constexpr int NT = 32;            // threads per CTA: one warp (its barriers are warp-wide)
 constexpr int RB = 8;             // consecutive slots per thread
 constexpr int NCAND = 120;        // longest Toeplitz candidate run kept in shared memory
 constexpr int SEGN = TS + NCAND + 8;
 static_assert(SEGN % 8 == 0, "staging layout works on rows of 8 pixels");
 static_assert(TS == NT * RB, "tile = threads x slots per thread");
-constexpr int TOE_CTAS_PER_SM = 6;  // resident CTAs of the Toeplitz kernels (registers and shared memory)
+constexpr int TOE_CTAS_PER_SM = 11; // resident CTAs of the Toeplitz kernels (shared memory: 11 x 19 KB)
 
 // shared-memory position of staged pixel m: rows of eight 16-byte pixels
 // (128 bytes, every bank once), the pixel's slot within its row XOR-ed with
@@ -289,10 +289,10 @@ __device__ __forceinline__ int ring_range_count(const int32_t *pre, int start, i
 // Steps are unrolled by eight so that the register of every pixel is fixed
 // at compile time (no moves).  Per ring pair the CTA stages, with cp.async
 // into a double buffer, the bin-ring segment the tile needs (16-byte pixels
-// in the XOR-swizzled row layout of tpos), the per-offset geometry and the
-// prefix counts of the segment (eight planes, conflict-free for the stride-8
-// slots); ring pair e + 1 is in flight while e is summed.  Tiles of other
-// rings are skipped (the general kernel has them).
+// in the XOR-swizzled row layout of tpos) and the per-offset geometry; ring
+// pair e + 1 is in flight while e is summed.  The galaxy counts of the
+// windows are differences of the count prefix, read from global memory.
+// Tiles of other rings are skipped (the general kernel has them).
 // ------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -308,12 +308,6 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // floor(a / b) for -b <= a < 2b
 __device__ __forceinline__ int wraps(int a, int b) { return a < 0 ? -1 : (a >= b ? 1 : 0); }
 
-constexpr int PREN = SEGN + 8;
-constexpr int PSTR = PREN / 8;        // prefix counts in 8 planes: m -> (m & 7) * PSTR + (m >> 3); a warp
-                                      // reads one plane at consecutive positions
-static_assert(PREN % 8 == 0, "prefix planes");
-
-__device__ __forceinline__ int ppos(int m) { return (m & 7) * PSTR + (m >> 3); }
 
 // what a tile needs of one of its ring pairs; the tile's first TPN ring
 // pairs are read into shared memory once, at the start of the tile
@@ -345,8 +339,7 @@ __device__ __forceinline__ ToeStage tile_param(const MapArgs &a, const ToeStage 
 
 // issue the copies of ring pair e of a tile into buffer b
 __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par, int64_t row0, int e, int jbase,
-                                          int nslots, float4 (*seg)[SEGN], float4 (*geo)[NCAND], int (*pre)[8 * PSTR],
-                                          int b, int tid) {
+                                          int nslots, float4 (*seg)[SEGN], float4 (*geo)[NCAND], int b, int tid) {
     const ToeStage t = tile_param(a, par, row0, e, jbase);
     if (t.L > 0) {
         const int nseg = min(SEGN, nslots + t.L + 7);
@@ -357,12 +350,6 @@ __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par,
             cp_async16(&seg[b][tpos(m)], a.PX + t.start + kk);
         }
         for (int c = tid; c < t.L; c += NT) cp_async16(&geo[b][c], a.toe_geo + t.off + t.da + c);
-        const int npre = min(PREN, nslots + t.L + 1);
-        for (int m = tid; m < npre; m += NT) {
-            int kk = t.k0 + m;
-            kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
-            cp_async4(&pre[b][ppos(m)], a.NPRE + t.start + kk);
-        }
     }
     cp_async_commit();
 }
@@ -370,7 +357,6 @@ __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par,
 struct ToeShared {
     float4 seg[2][SEGN];
     float4 geo[2][NCAND];
-    int pre[2][8 * PSTR];
     int slot_t[TS];
     ToeStage par[TPN];
 };
@@ -406,7 +392,6 @@ template <int KIND>
 __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, ToeShared &S) {
     auto &seg = S.seg;
     auto &geo = S.geo;
-    auto &pre = S.pre;
     auto &slot_t = S.slot_t;
     const int tid = threadIdx.x;
     const int64_t tb = a.tiles[tile], te = a.tiles[tile + 1];
@@ -422,7 +407,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
     for (int64_t t = tb + tid; t < te; t += NT) slot_t[(int)(a.targets[t] - ring_start0) - jbase] = (int)(t - tb);
     __syncthreads();      // slot map and ring-pair parameters written
 
-    toe_stage(a, S.par, row0, 0, jbase, nslots, seg, geo, pre, 0, tid);
+    toe_stage(a, S.par, row0, 0, jbase, nslots, seg, geo, 0, tid);
 
     const int s0 = RB * tid;
     bool any = false;
@@ -442,7 +427,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
         const int b = e & 1;
         cp_async_wait_all();
         __syncthreads();       // ring pair e staged; everyone is done with buffer b ^ 1
-        if (e + 1 < nent) toe_stage(a, S.par, row0, e + 1, jbase, nslots, seg, geo, pre, b ^ 1, tid);
+        if (e + 1 < nent) toe_stage(a, S.par, row0, e + 1, jbase, nslots, seg, geo, b ^ 1, tid);
         const ToeStage cur = tile_param(a, S.par, row0, e, jbase);
         const int L = cur.L;
         if (L > 0 && any) {
@@ -480,18 +465,32 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                     }
                 }
             }
-            // galaxies in [k0 + s, k0 + s + L) from the staged prefix, with the
-            // ring total added for every pass over the ring's end
-            const int *pr = pre[b];
-            const bool seam = cur.k0 + s0 < 0 || cur.k0 + s0 + RB - 1 + L >= cur.nr;
+            // galaxies of the slots' windows [k0 + s, k0 + s + L) from the
+            // count prefix in global memory: after the pairs (the window never
+            // passes the ring's end more than once; tiles at the seam take the
+            // wrapped indices)
+            const int lo0 = cur.k0 + s0;
+            const bool seam = lo0 < 0 || lo0 + RB - 1 + L >= cur.nr;
+            int pa[RB], pz[RB];
+            if (!seam) {
+                const int32_t *pp = a.NPRE + cur.start + lo0;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    pa[r] = __ldg(pp + r);
+                    pz[r] = __ldg(pp + r + L);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int lo = lo0 + r, hi = lo + L;
+                    const int klo = lo - wraps(lo, cur.nr) * cur.nr, khi = hi - wraps(hi, cur.nr) * cur.nr;
+                    pa[r] = __ldg(a.NPRE + cur.start + klo);
+                    pz[r] = __ldg(a.NPRE + cur.start + khi) + (wraps(hi, cur.nr) - wraps(lo, cur.nr)) * cur.tot;
+                }
+            }
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
-                int n = pr[ppos(s0 + r + L)] - pr[ppos(s0 + r)];
-                if (seam) {
-                    const int lo = cur.k0 + s0 + r;
-                    n += (wraps(lo + L, cur.nr) - wraps(lo, cur.nr)) * cur.tot;
-                }
-                NN[r] += n;
+                NN[r] += pz[r] - pa[r];
                 NM[r] += L;
             }
             if ((e & 1) || e + 1 == nent) {
