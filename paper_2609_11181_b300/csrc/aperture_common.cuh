@@ -69,6 +69,7 @@ struct MapArgs {
     int32_t *members;
     unsigned long long *fp64_count;
     int *status;             // device status word (SMART_STATUS_* bits)
+    float pixrad;            // largest angular radius of a bin pixel (rad)
 };
 
 // great-circle separation^2 from the chord^2: d^2 = sum_n 2 s^(2n) / (n^2 C(2n,n))

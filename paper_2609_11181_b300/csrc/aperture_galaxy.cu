@@ -50,7 +50,31 @@ __device__ __forceinline__ GalRing gal_ring(const RingPair &Rp) {
 }
 
 // galaxy-only part of the pair geometry; frg = the galaxy's azimuth on the
-// bin-ring lattice minus its pixel index kg
+// bin-ring lattice minus its pixel index kg.  MODE 0: |dl| <= 0.05 rad, two
+// series terms (truncation below 6e-8 relative); otherwise as below.
+template <int MODE>
+__device__ __forceinline__ void gal_setup_m(const GalRing &R, const float4 &geo, float &A, float &B, float &C,
+                                            float &D, float &frg) {
+    const float dl = R.dlat - geo.x;
+    if (MODE == 0) {
+        const float d2 = dl * dl;
+        A = d2 * fmaf(d2, -1.0f / 12.0f, 1.0f);
+        C = dl * fmaf(d2, -1.0f / 6.0f, 1.0f);
+    } else if (MODE == 1) {
+        const float d2 = dl * dl;
+        A = d2 * fmaf(d2, fmaf(d2, 1.0f / 360.0f, -1.0f / 12.0f), 1.0f);
+        C = dl * fmaf(d2, fmaf(d2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    } else {
+        float sdh, cdh;
+        sincosf(0.5f * dl, &sdh, &cdh);
+        A = 4.0f * sdh * sdh;
+        C = 2.0f * sdh * cdh;
+    }
+    B = R.B0 * geo.w;
+    D = R.D0 * geo.z;
+    frg = geo.y + R.fr_shift;
+}
+
 __device__ __forceinline__ void gal_setup(const GalRing &R, const float4 &geo, float &A, float &B, float &C,
                                           float &D, float &frg) {
     const float dl = R.dlat - geo.x;
@@ -128,16 +152,43 @@ struct BandPair {
     int32_t entry;      // ring-pair entry of the target's output ring
 };
 
+// azimuth offset of a galaxy from a target in bin pixels; a wide ring pair
+// (the union window may span most of the ring) wraps it into [-nr/2, nr/2]
+template <int MODE>
+__device__ __forceinline__ float gal_du(float Gp, float Tr, const GalRing &R) {
+    float d = Gp - Tr;
+    if (MODE == 2) {
+        const float nr = (float)R.nr, half = 0.5f * (float)R.nr;
+        d = d > half ? d - nr : (d < -half ? d + nr : d);
+    }
+    return d;
+}
+
+// great-circle separation^2 from the chord^2 for chords below 0.05 (two
+// series terms: truncation below 4e-5 of the next term's 1e-8)
+__device__ __forceinline__ float sep2_short(float s2) { return s2 * fmaf(s2, 1.0f / 12.0f, 1.0f); }
+
 // The galaxies of one ring pair's union window for the warp's targets: lanes
 // stride over the contiguous galaxy runs; each galaxy record serves every
-// target.  The per-target body has no branch on membership (non-members add
-// zeros), so the GT independent chains can interleave; guard-band pairs take
-// a rare branch to the float64 list.
-template <int KIND, bool SMALL, bool BARY>
+// target.  The azimuth offset of a galaxy from a target is formed from
+// small exact numbers: the galaxy's pixel position within the union window
+// (an integer below the window length) plus its offset inside the pixel,
+// minus the target's lattice position relative to the window start, so its
+// float32 rounding stays below 3e-7 of the window's half width -- far inside
+// the guard band.  The per-target body has no branch (non-members add zeros
+// through a 0/1 factor); a galaxy whose chord^2 to any target lies inside the
+// guard band takes one rare branch to the float64 list.  Targets past the
+// group's end sit far away (never members).  MODE picks the series: 0 when
+// every |u| and |dl| of the ring pair stays below 0.05 rad, 1 below 0.45,
+// 2 beyond.
+template <int KIND, int MODE, bool BARY>
 __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba, const RingPair &Rp, const GalRing &R,
-                                            int e, int lane, int64_t tb, const bool (&on)[GT], const int (&Xi)[GT],
-                                            const float (&Xf)[GT], int lo, int len, float (&pe)[GT], float (&pb)[GT],
-                                            float (&pv)[GT], float (&pw)[GT], int (&nn)[GT], int (&nm)[GT]) {
+                                            int e, int lane, int64_t tb, const float (&Tr)[GT],
+                                            const float (&onf)[GT], int lo, int len,
+                                            float (&pe)[GT], float (&pb)[GT], float (&pv)[GT], float (&pw)[GT],
+                                            float (&nf)[GT], int (&nn)[GT], int (&nm)[GT]) {
+    // a generous pre-filter for the guard band; the exact test follows
+    const float Tmid = 0.5f * (a.Tlo + a.Thi), Thw = 0.5f * (a.Thi - a.Tlo) * 1.001f;
     const int n1 = min(len, Rp.nr - lo);
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
@@ -146,42 +197,64 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
         if (pn <= 0) continue;
         const int g0 = __ldg(a.offsets + R.start + pa);
         const int g1 = __ldg(a.offsets + R.start + pa + pn);
+        // union-window position of pixel kg: kg - lo (part 0) or kg + n1 (part 1)
+        const int kshift = part == 0 ? -(R.start + lo) : n1 - R.start;
 #pragma unroll 1
         for (int g = g0 + lane; g < g1; g += 32) {
             const float4 geo = __ldg(a.geo + g);
             const float4 sh = __ldg(a.shear + g);
-            const int kg = (int)__ldg(a.keys + g) - R.start;
+            const int krel = (int)__ldg(a.keys + g) + kshift;
             const int cnt = BARY ? __ldg(ba.cnt + g) : 1;
             float A, B, C, D, frg;
-            gal_setup(R, geo, A, B, C, D, frg);
-            unsigned band = 0;       // targets for which this galaxy lies in the guard band
+            gal_setup_m<MODE>(R, geo, A, B, C, D, frg);
+            const float Gp = (float)krel + frg;          // galaxy on the window's lattice
+            float dmin = 3.0e38f;
 #pragma unroll
             for (int r = 0; r < GT; ++r) {
-                const float u = gal_u(R, kg, frg, Xi[r], Xf[r]);
+                const float u = gal_du<MODE>(Gp, Tr[r], R) * R.dphi;
                 float sinu, h;
-                if (SMALL) sin_hav_small(u, sinu, h);
+                if (MODE == 0) sin_hav_narrow(u, sinu, h);
+                else if (MODE == 1) sin_hav_small(u, sinu, h);
                 else sin_hav_wide(u, sinu, h);
                 const float s2 = fmaf(B, h, A);
-                const bool in = on[r] && s2 < a.Tlo;
-                band |= (on[r] && !(s2 < a.Tlo) && s2 <= a.Thi) ? (1u << r) : 0u;
+                const float m = s2 < a.Tlo ? onf[r] : 0.0f;
+                dmin = fminf(dmin, fabsf(s2 - Tmid));
                 const float x = R.mrho0 * sinu;
                 const float y = fmaf(D, h, C);
                 const float xx = x * x;
                 const float sd2 = fmaf(y, y, xx);
                 const float cc = fmaf(y, y, -xx);
                 const float ss = -2.0f * x * y;
-                const float Q = filter_Q<KIND>(a.f, a.f.qtab, s2);
-                const float w = (in && sd2 > 1e-30f) ? __fdividef(Q, sd2) : 0.f;
+                float Q;
+                if (KIND == SMART_FILTER_POLY && MODE == 0) {
+                    const float X2 = sep2_short(s2) * a.f.inv_ap2;
+                    Q = a.f.qnorm * X2 * (1.0f - X2);
+                } else {
+                    Q = filter_Q<KIND>(a.f, a.f.qtab, s2);
+                }
+                const float wq = m * Q;
+                // sd2 = 0 only for a galaxy at the target's centre, where cc = ss = 0
+                const float w = __fdividef(wq, sd2 + 1e-30f);
                 pe[r] = fmaf(w, fmaf(sh.x, cc, sh.y * ss), pe[r]);
                 pb[r] = fmaf(w, fmaf(sh.y, cc, -sh.x * ss), pb[r]);
-                pv[r] = fmaf(in ? Q * Q : 0.f, sh.w, pv[r]);
-                pw[r] += in ? sh.z : 0.f;
-                nn[r] += in ? cnt : 0;
-                if (BARY) nm[r] += in ? 1 : 0;
+                pv[r] = fmaf(wq * Q, sh.w, pv[r]);
+                pw[r] = fmaf(m, sh.z, pw[r]);
+                if (BARY) {
+                    nn[r] += m != 0.f ? cnt : 0;
+                    nm[r] += m != 0.f ? 1 : 0;
+                } else {
+                    nf[r] += m;
+                }
             }
-            if (band) {              // rare: one branch per galaxy, not per pair
+            if (dmin <= Thw) {         // rare: one branch per galaxy, not per pair
                 for (int r = 0; r < GT; ++r) {
-                    if (!(band & (1u << r))) continue;
+                    const float u = gal_du<MODE>(Gp, Tr[r], R) * R.dphi;
+                    float sinu, h;
+                    if (MODE == 0) sin_hav_narrow(u, sinu, h);
+                    else if (MODE == 1) sin_hav_small(u, sinu, h);
+                    else sin_hav_wide(u, sinu, h);
+                    const float s2 = fmaf(B, h, A);
+                    if (onf[r] == 0.0f || s2 < a.Tlo || s2 > a.Thi) continue;
                     const unsigned long long slot = atomicAdd(a.band_count, 1ull);
                     if (slot < (unsigned long long)a.band_cap) {
                         BandPair bp;
@@ -207,10 +280,13 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a, cons
     const int64_t ring_start0 = a.targets[tb] - tr0.j0;
     int j0[GT];
     bool on[GT];
+    float onf[GT];
+    const int jlast = (int)(a.targets[tb + nt - 1] - ring_start0);
 #pragma unroll
     for (int r = 0; r < GT; ++r) {
         on[r] = r < nt;
-        j0[r] = on[r] ? (int)(a.targets[tb + r] - ring_start0) : tr0.j0;
+        onf[r] = on[r] ? 1.0f : 0.0f;
+        j0[r] = on[r] ? (int)(a.targets[tb + r] - ring_start0) : jlast;
     }
     float SE[GT], cSE[GT], SB[GT], cSB[GT], SV[GT], SW[GT], cSW[GT];
     int NN[GT], NM[GT];
@@ -246,26 +322,35 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a, cons
             ulo = 0;
             uhi = Rp.nr - 1;
         }
-        float pe[GT], pb[GT], pv[GT], pw[GT];
+        float pe[GT], pb[GT], pv[GT], pw[GT], nf[GT];
         int nn[GT], nm[GT];
+        // targets on the union window's lattice; a slot past the group's end
+        // repeats the last target, and its 0/1 factor is 0
+        float Tr[GT];
 #pragma unroll
         for (int r = 0; r < GT; ++r) {
-            pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
+            pe[r] = pb[r] = pv[r] = pw[r] = nf[r] = 0.f;
             nn[r] = nm[r] = 0;
+            Tr[r] = (float)(Xi[r] - ulo) + Xf[r];
         }
         // pixel range [ulo, uhi] -> at most two runs of ring pixels
         // ulo lies in (-nr, 2 nr): one correction brings it into [0, nr)
         const int lo = ulo < 0 ? ulo + Rp.nr : (ulo >= Rp.nr ? ulo - Rp.nr : ulo);
         const int len = uhi - ulo + 1;
-        if (R.small) gal_segment<KIND, true, BARY>(a, ba, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn, nm);
-        else gal_segment<KIND, false, BARY>(a, ba, Rp, R, e, lane, tb, on, Xi, Xf, lo, len, pe, pb, pv, pw, nn, nm);
+        // series by the largest |u| (window plus one pixel) and |dl| (ring
+        // offset plus a bin pixel's half extent) of the ring pair
+        const int mode = (Rp.flags & RP_WIDE) ? 2
+                         : ((float)(len + 2) * Rp.dphi <= 0.05f && fabsf(Rp.dlat) + a.pixrad <= 0.05f) ? 0 : 1;
+        if (mode == 0) gal_segment<KIND, 0, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);
+        else if (mode == 1) gal_segment<KIND, 1, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);
+        else gal_segment<KIND, 2, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);
 #pragma unroll
         for (int r = 0; r < GT; ++r) {
             kahan_add(SE[r], cSE[r], pe[r]);
             kahan_add(SB[r], cSB[r], pb[r]);
             SV[r] += pv[r];
             kahan_add(SW[r], cSW[r], pw[r]);
-            NN[r] += nn[r];
+            NN[r] += BARY ? nn[r] : (int)nf[r];
             NM[r] += nm[r];
         }
     }
@@ -531,6 +616,7 @@ static smart_status map_records(smart_ctx *c, const smart_maps *out, bool bary) 
     a.table = c->rp_gal;
     a.counts = c->rp_gal_cnt;
     a.kmax = c->kmax_gal;
+    a.pixrad = (float)(max_pixrad(c->nside_bin) * 1.01);
     a.offsets = bary ? c->bary_off : c->offsets;
     a.geo = bary ? c->bary_geo : c->rec_geo;
     a.shear = bary ? c->bary_sh : c->rec_shear;
