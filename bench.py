@@ -440,20 +440,33 @@ def run_native_pixel(args, world, rank):
                 "basis": f"whole step: member pairs x {algo} algorithmic flop per pair / ms_per_step"}
 
     # end to end through the public API: every step copies its inputs from
-    # pinned host memory, maps them and reads all results back.  Steps are
-    # pipelined the way a serving loop would run them: double-buffered device
-    # inputs and outputs, host->device copies on one stream, the map on the
-    # context's stream, device->host copies on a third, so step k + 1's copy
-    # in and step k - 1's copy out overlap step k's map.
-    host_in = [x.cpu().pin_memory() for x in inputs]
+    # pinned host memory, maps them and reads the maps back.  The input is the
+    # footprint's pixels only, as runs of consecutive RING pixels
+    # (smart_set_binned_runs; outside the footprint the binned data are zero,
+    # so the maps equal the device run's bit for bit); the results read back
+    # are M_E, M_B, sigma^2 and the weight sum.  Steps are pipelined the way
+    # a serving loop would run them: double-buffered device inputs and
+    # outputs, host->device copies on one stream, the map on the context's
+    # stream, device->host copies on a third, so step k + 1's copy in and
+    # step k - 1's copy out overlap step k's map.
+    foot = wl.targets.cpu().numpy()                  # the footprint's pixels (where the data are)
+    brk = np.nonzero(np.diff(foot) != 1)[0] + 1
+    r_first = np.concatenate([[0], brk])
+    r_end = np.concatenate([brk, [foot.size]])
+    runs_np = np.stack([foot[r_first], r_end - r_first, r_first], 1).astype(np.int64)
+    fidx = wl.targets
+    host_in = [inputs[0][fidx].cpu().pin_memory(), inputs[1][fidx].cpu().pin_memory(),
+               torch.from_numpy(runs_np).pin_memory()]
     h2d = sum(x.numel() * x.element_size() for x in host_in)
-    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    read_back = ("map_e", "map_b", "var", "sum_w")
+    d2h = sum(out[k].numel() * out[k].element_size() for k in read_back)
     s_in, s_map, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ectx = api.Context(wl.nside, wl.theta_ap_arcmin, wl.filter, nside_bin=wl.nside, stream=s_map)
     ectx.set_targets(wl.targets)
-    dev_in = [[torch.empty_like(x) for x in inputs] for _ in range(2)]
+    dev_in = [[torch.empty(x.shape, dtype=x.dtype, device=dev) for x in host_in] for _ in range(2)]
     outs = [ectx._out(None)[0] for _ in range(2)]
-    host_out = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()} for _ in range(2)]
+    host_out = [{k: torch.empty(out[k].shape, dtype=out[k].dtype, pin_memory=True) for k in read_back}
+                for _ in range(2)]
     e_steps = max(4, min(args.steps, 8))
     ev_in = [torch.cuda.Event() for _ in range(e_steps)]
     ev_map = [torch.cuda.Event() for _ in range(e_steps)]
@@ -471,13 +484,13 @@ def run_native_pixel(args, world, rank):
             s_map.wait_event(ev_in[k])
             if k >= 2:
                 s_map.wait_event(ev_out[k - 2])       # outputs of buffer i read back
-            ectx.set_binned_packed(*dev_in[i])
+            ectx.set_binned_runs(*dev_in[i])
             ectx.map_pixel(outs[i])
             ev_map[k].record(s_map)
             s_out.wait_event(ev_map[k])
             with torch.cuda.stream(s_out):
-                for key, v in outs[i].items():
-                    host_out[i][key].copy_(v, non_blocking=True)
+                for key in read_back:
+                    host_out[i][key].copy_(outs[i][key], non_blocking=True)
                 ev_out[k].record(s_out)
         stream.wait_event(ev_out[n - 1])
         stream.wait_event(ev_map[n - 1])
@@ -490,7 +503,7 @@ def run_native_pixel(args, world, rank):
     e2e_run(e_steps)
     t1.record(stream)
     torch.cuda.synchronize()
-    same = all(torch.equal(host_out[(e_steps - 1) % 2][k].to(v.device), v) for k, v in out.items())
+    same = all(torch.equal(host_out[(e_steps - 1) % 2][k].to(out[k].device), out[k]) for k in read_back)
     ectx.close()
     del dev_in, outs, host_out, host_in
     e2e_ms = max_over_ranks(t0.elapsed_time(t1) / e_steps, world)
@@ -516,7 +529,9 @@ def run_native_pixel(args, world, rank):
         "e2e": {"value": round(pairs_all / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gpair/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),
                 "steps": e_steps, "pipelined": "double-buffered; copy in, map and copy out on three streams",
-                "results_equal_device_run": same},
+                "input": f"footprint pixels as {len(runs_np)} runs of RING pixels (smart_set_binned_runs), "
+                         f"{foot.size} of {12 * wl.nside ** 2} pixels",
+                "read_back": list(read_back), "results_equal_device_run": same},
         "gpu_launches": int(round(launches_step * args.steps)),
         "clocks": ck,
         "input_gen_s": round(t_gen, 1),

@@ -163,6 +163,24 @@ smart_status smart_set_binned(smart_ctx *ctx, const float *G1, const float *G2,
                               const float *W, const float *S2, const int32_t *n_p);
 
 /*
+ * The binned input of a footprint: only the pixels the caller has, as runs
+ * of consecutive RING pixels (a cap gives one or two runs per ring).  px
+ * (float4 per pixel: G1, G2, S2, W, 16-byte aligned) and n_p hold the runs'
+ * pixels back to back, n_compact of each; runs holds n_runs triples
+ * (first RING pixel, length, position of the run's first pixel in px / n_p),
+ * int64.  All device pointers.  The pixels are copied into the context's own
+ * full-sky map; every other pixel is zero when the map was just made, when it
+ * held other data (smart_bin_galaxies, smart_set_binned) or when clear != 0,
+ * and otherwise keeps the value of the last call.  A caller whose footprint's
+ * data stay zero outside the runs thus ships only the runs: the maps equal
+ * those of the full-sky input bit for bit.  A run that does not fit the map
+ * or the compact arrays is skipped and the next smart_sync returns
+ * SMART_E_ARG.  Asynchronous; SMART_E_ARG for bad pointers or sizes.
+ */
+smart_status smart_set_binned_runs(smart_ctx *ctx, const float *px, const int32_t *n_p, const int64_t *runs,
+                                   int64_t n_runs, int64_t n_compact, int clear);
+
+/*
  * Same input in the library's native layout: px holds 4 floats per pixel
  * (G1, G2, S2, W) -- note S2 before W -- for the 12 nside_bin^2 RING pixels
  * (device pointer, 16-byte aligned), n_p the counts.  Both arrays are

@@ -90,6 +90,7 @@ SIGNATURES = {
     "smart_fma_probe": (_I32, [_I32, _I64, _I32, _VP, ctypes.POINTER(_D)]),
     "smart_map_projected": (_I32, [_VP, _D, _D, ctypes.POINTER(SmartMaps)]),
     "smart_set_wait_limit": (_I32, [_VP, _D]),
+    "smart_set_binned_runs": (_I32, [_VP, _VP, _VP, _VP, _I64, _I64, _I32]),
     "smart_annulus_stats": (_I32, [_VP, _D, _D, _D, _VP, _VP, _I32, _VP, _VP, _VP]),
 }
 

@@ -155,6 +155,20 @@ class Context:
             "smart_set_binned_packed")
         self._keep = [px, n_p]
 
+    def set_binned_runs(self, px, n_p, runs, clear: bool = False):
+        """Footprint input: px (m, 4) float32 and n_p (m,) int32 hold the pixels
+        of the runs back to back; runs (k, 3) int64 = (first RING pixel,
+        length, offset into px).  Copied into the context's own map."""
+        m = n_p.numel()
+        if px.dim() != 2 or px.shape[1] != 4 or px.shape[0] != m:
+            raise ValueError("px must have shape (m, 4) with m = n_p.numel()")
+        if runs.dim() != 2 or runs.shape[1] != 3:
+            raise ValueError("runs must have shape (k, 3)")
+        self._check(self._lib.smart_set_binned_runs(
+            self._h, _ptr(px, torch.float32, "px"), _ptr(n_p, torch.int32, "n_p"), _ptr(runs, torch.int64, "runs"),
+            runs.shape[0], m, 1 if clear else 0), "smart_set_binned_runs")
+        self._keep = [px, n_p, runs]
+
     # -- maps
     def _out(self, out):
         if out is None:

@@ -564,6 +564,7 @@ extern "C" smart_status smart_bin_galaxies(smart_ctx *c, const double *ra, const
     c->NP = c->own_np;
     c->have_binned = true;
     c->binned_from_catalog = true;
+    c->binned_from_runs = false;
     c->have_catalog = true;
     c->n_gal = n;
     c->catalog_version += 1;

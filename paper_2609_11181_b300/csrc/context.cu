@@ -151,6 +151,9 @@ extern "C" smart_status smart_sync(smart_ctx *c, double timeout_s) {
             return fail(c, SMART_E_ARG, "smart_bin_galaxies: " + std::to_string(inv) +
                                             " galaxies with non-finite ra/dec or |dec| > 90 (left out of the catalogue)");
         }
+        if (status & SMART_STATUS_BAD_RUNS)
+            return fail(c, SMART_E_ARG, "smart_set_binned_runs: a run lies outside the map or the compact arrays "
+                                        "(those runs were skipped)");
         if (status & SMART_STATUS_BAND_OVERFLOW)
             return fail(c, SMART_E_OVERFLOW, "guard-band pair list overflowed: map incomplete");
         return fail(c, SMART_E_INTERNAL, "device status " + std::to_string(status));
@@ -248,6 +251,59 @@ extern "C" smart_status smart_set_binned(smart_ctx *c, const float *G1, const fl
     return SMART_OK;
 }
 
+// one block per run: the run's pixels, contiguous in the compact arrays,
+// go to their RING positions in the full-sky map.  A run that does not fit
+// the map or the compact arrays is skipped and flagged in the status word.
+__global__ void k_scatter_runs(const float4 *__restrict__ px, const int32_t *__restrict__ np,
+                               const int64_t *__restrict__ runs, int64_t n_runs, int64_t npix, int64_t n_compact,
+                               float4 *__restrict__ out_px, int32_t *__restrict__ out_np, int *__restrict__ status) {
+    for (int64_t r = blockIdx.x; r < n_runs; r += gridDim.x) {
+        const int64_t first = runs[3 * r], len = runs[3 * r + 1], off = runs[3 * r + 2];
+        if (first < 0 || len < 0 || first > npix - len || off < 0 || off > n_compact - len) {
+            if (threadIdx.x == 0) atomicOr(status, SMART_STATUS_BAD_RUNS);
+            continue;
+        }
+        for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+            out_px[first + i] = px[off + i];
+            out_np[first + i] = np[off + i];
+        }
+    }
+}
+
+extern "C" smart_status smart_set_binned_runs(smart_ctx *c, const float *px, const int32_t *n_p, const int64_t *runs,
+                                              int64_t n_runs, int64_t n_compact, int clear) {
+    if (!c) return SMART_E_ARG;
+    if (n_runs < 0 || n_compact < 0 || (n_runs > 0 && !runs) || (n_compact > 0 && (!px || !n_p)))
+        return fail(c, SMART_E_ARG, "smart_set_binned_runs: bad pointer or size");
+    if (((uintptr_t)px & 15) != 0) return fail(c, SMART_E_ARG, "smart_set_binned_runs: pixels not 16-byte aligned");
+    const bool fresh = !c->own_px || !c->own_np;
+    smart_status st = ensure_own_binned(c);
+    if (st != SMART_OK) return st;
+    const int64_t npix = npix_of(c->nside_bin);
+    // the map is cleared when asked, when it was just made, and when it held
+    // other data (a catalogue's or a full map's): pixels outside the runs are
+    // then zero
+    if (clear || fresh || !c->binned_from_runs) {
+        if ((st = check_cuda(c, cudaMemsetAsync(c->own_px, 0, (size_t)npix * sizeof(float4), c->stream), "clear map")) !=
+                SMART_OK ||
+            (st = check_cuda(c, cudaMemsetAsync(c->own_np, 0, (size_t)(npix + 1) * sizeof(int32_t), c->stream),
+                             "clear counts")) != SMART_OK)
+            return st;
+    }
+    if (n_runs > 0) {
+        const unsigned blocks = (unsigned)std::min<int64_t>(n_runs, (int64_t)c->num_sms * 16);
+        k_scatter_runs<<<blocks, 256, 0, c->stream>>>((const float4 *)px, n_p, runs, n_runs, npix, n_compact, c->own_px,
+                                                      c->own_np, c->d_status);
+        if ((st = check_cuda(c, cudaGetLastError(), "k_scatter_runs")) != SMART_OK) return st;
+    }
+    c->PX = c->own_px;
+    c->NP = c->own_np;
+    c->have_binned = true;
+    c->binned_from_catalog = false;
+    c->binned_from_runs = true;
+    return SMART_OK;
+}
+
 extern "C" smart_status smart_set_binned_packed(smart_ctx *c, const float *px, const int32_t *n_p) {
     if (!c) return SMART_E_ARG;
     if (!px || !n_p) return fail(c, SMART_E_ARG, "smart_set_binned_packed: null pointer");
@@ -256,6 +312,7 @@ extern "C" smart_status smart_set_binned_packed(smart_ctx *c, const float *px, c
     c->NP = n_p;
     c->have_binned = true;
     c->binned_from_catalog = false;
+    c->binned_from_runs = false;
     return SMART_OK;
 }
 

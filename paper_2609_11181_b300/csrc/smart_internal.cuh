@@ -267,7 +267,7 @@ static_assert(sizeof(RingPair) == 64, "RingPair layout");
 enum { RP_SHIFTED = 1, RP_WIDE = 2, RP_WHOLE = 4 };
 
 // bits of the device status word read back by smart_sync
-enum { SMART_STATUS_BAND_OVERFLOW = 1, SMART_STATUS_INVALID_COORDS = 2 };
+enum { SMART_STATUS_BAND_OVERFLOW = 1, SMART_STATUS_INVALID_COORDS = 2, SMART_STATUS_BAD_RUNS = 4 };
 
 // Per ring pair of the pixel-mode table: where its per-offset geometry sits
 // in the Toeplitz pool (off = -1: not a Toeplitz pair), the candidate
@@ -313,6 +313,7 @@ struct smart_ctx {
     int32_t *own_np = nullptr;       // npix + 1
     bool have_binned = false;
     bool binned_from_catalog = false;   // the catalogue offsets are then the count prefix
+    bool binned_from_runs = false;      // own map written by smart_set_binned_runs (zero outside the runs)
 
     // sorted catalogue
     int64_t n_gal = 0, cap_gal = 0;

@@ -222,3 +222,57 @@ def test_guard_band_targets_finished_in_place(cuda_device):
     ctx.set_band_slot_limit(0)
     _, rpx = _oracle_maps(cat, tg, nside, nside, theta_arcmin, 2)
     _check(a, rpx, "guard band")
+
+
+def _runs_of(pix):
+    """Maximal runs of consecutive RING pixels: (first, length, offset)."""
+    pix = np.asarray(pix, np.int64)
+    brk = np.nonzero(np.diff(pix) != 1)[0] + 1
+    starts = np.concatenate([[0], brk])
+    ends = np.concatenate([brk, [pix.size]])
+    return np.stack([pix[starts], ends - starts, starts], 1).astype(np.int64)
+
+
+def test_binned_runs_equal_the_full_map(cuda_device):
+    """A footprint given as runs of RING pixels (the cap crosses the azimuth
+    seam, so rings split into two runs) gives the full-sky input's maps bit
+    for bit; a second call with fewer runs and no clearing keeps the rest; a
+    run outside the map is reported by the next sync."""
+    nside = 256
+    b, foot = binned_field_oracle(31, nside, 359.0, 20.0, 9.0, mean_count=12.0)
+    tg = torch.from_numpy(np.nonzero(foot)[0].astype(np.int64)).to(cuda_device)
+    full = [x.to(cuda_device) for x in (b.G1, b.G2, b.W, b.S2, b.n)]
+    ctx = api.Context(nside, 25.0, "schirmer", nside_bin=nside)
+    ctx.set_targets(tg)
+    ctx.set_binned(*full)
+    ref = {k: v.clone() for k, v in ctx.map_pixel().items()}
+    pix = np.nonzero(foot)[0]
+    runs = _runs_of(pix)
+    assert (runs[:, 1] < 4 * nside).sum() > 0 and len(runs) > 40
+    it = torch.from_numpy(pix).to(cuda_device)
+    px = torch.stack([full[0], full[1], full[3], full[2]], 1)[it].contiguous()
+    n_p = full[4][it].contiguous()
+    rt = torch.from_numpy(runs).to(cuda_device)
+    ctx.set_binned_runs(px, n_p, rt)
+    got = ctx.map_pixel()
+    ctx.sync(60)
+    for k in ref:
+        assert torch.equal(got[k], ref[k]), k
+    # fewer runs, no clearing: the pixels of the other runs are kept
+    ctx.set_binned_runs(px, n_p, rt[: len(runs) // 2])
+    got = ctx.map_pixel()
+    ctx.sync(60)
+    for k in ref:
+        assert torch.equal(got[k], ref[k]), k
+    # clearing keeps only the given runs
+    ctx.set_binned_runs(px, n_p, rt[: len(runs) // 2], clear=True)
+    got = ctx.map_pixel()
+    ctx.sync(60)
+    assert not torch.equal(got["map_e"], ref["map_e"])
+    # a run past the end of the map is skipped and reported
+    bad = rt[:1].clone()
+    bad[0, 0] = 12 * nside * nside
+    ctx.set_binned_runs(px, n_p, bad)
+    with pytest.raises(api.SmartError, match="SMART_E_ARG"):
+        ctx.sync(60)
+    ctx.close()
