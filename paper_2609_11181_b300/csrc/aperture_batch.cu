@@ -113,7 +113,7 @@ struct smart_batch {
     cudaGraphExec_t exec = nullptr;
     bool own_stream = false;
     int kind = 0;
-    int ctas_per_sm = 8;
+    int ctas_per_sm = TOE_CTAS_PER_SM;
     int order = 0;            // 0: longest first, 1: natural
     double tuned_ms = 0.0;
     std::string err;
@@ -346,7 +346,8 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         double best = 1e30;
-        const int shapes[] = {4, 6, 8};
+        // resident one-warp CTAs per SM: the shared-memory limit, and fewer
+        const int shapes[] = {TOE_CTAS_PER_SM - 4, TOE_CTAS_PER_SM - 2, TOE_CTAS_PER_SM};
         for (int order = 0; order < 2 && st == SMART_OK; ++order) {
             for (int cps : shapes) {
                 st = batch_launch(b, cps, order);       // warm
