@@ -1020,6 +1020,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the other forms (brute force, batched, learned) after the headline")
+    ap.add_argument("--with-projected", action="store_true",
+                    help="galaxy workloads: also time the Cartesian projected map on the same catalogue")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1031,7 +1033,7 @@ def main():
     elif args.workload == "learned":
         res = run_native_learned(args, world, rank)
     elif args.workload in GALAXY_WORKLOADS:
-        res = run_native_galaxy(args, world, rank)
+        res = run_native_galaxy(args, world, rank, projected=args.with_projected)
     else:
         res = run_native_pixel(args, world, rank)
         if args.workload == "pixel4096" and world == 1 and not args.no_forms:
