@@ -217,12 +217,12 @@ def measure_fma_peaks(stream, target_ms=60.0, repeats=3):
     launches of about target_ms each after a warm-up.  Changes no clock or
     power setting."""
     out = {}
-    for bits in (32, 64):
+    for bits, packed, key in ((32, False, "fp32"), (32, True, "fp32x2"), (64, False, "fp64")):
         iters = 512 if bits == 32 else 16
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         while True:                                   # size the launch to about target_ms
             a.record(stream)
-            flops = api.fma_probe(bits, iters, 8, stream)
+            flops = api.fma_probe(bits, iters, 8, stream, packed)
             b.record(stream)
             b.synchronize()
             ms = a.elapsed_time(b)
@@ -233,15 +233,25 @@ def measure_fma_peaks(stream, target_ms=60.0, repeats=3):
         best = 0.0
         for _ in range(repeats):
             a.record(stream)
-            flops = api.fma_probe(bits, iters, 8, stream)
+            flops = api.fma_probe(bits, iters, 8, stream, packed)
             b.record(stream)
             b.synchronize()
             best = max(best, flops / (a.elapsed_time(b) * 1e-3) / 1e12)
-        out[f"fp{bits}_tflops"] = round(best, 3)
+        out[f"{key}_tflops"] = round(best, 3)
     out["how"] = ("library probe smart_fma_probe: 8 independent FMA chains per thread, 8 x 256-thread CTAs per SM, "
                   f"about {target_ms:.0f} ms per launch, best of {repeats} (CUDA events)")
     out["fp32_nominal_tflops"] = round(FP32_NOMINAL_TFLOPS, 2)
     return out
+
+
+def fp32_peak(peaks_live):
+    """The FP32 roofline denominator: the higher of the scalar and the packed
+    (two FMAs per instruction) probe rates, and where it comes from."""
+    sc, pk = peaks_live["fp32_tflops"], peaks_live.get("fp32x2_tflops", 0.0)
+    src = (f"FP32 FMA throughput measured in this run by the library's probe ({peaks_live['how']}): "
+           f"scalar FMA {sc}, packed two-lane FMA {pk}; the higher is the peak; "
+           f"nominal {FP32_NOMINAL_TFLOPS:.2f} (148 SMs x 128 lanes x 2 x 2032 MHz)")
+    return max(sc, pk), src
 
 
 def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_source: str):
@@ -424,9 +434,7 @@ def run_native_pixel(args, world, rank):
     pairs_all = sum_over_ranks(float(pairs_step), world)
     value = pairs_all / (ms_step * 1e-3) / 1e9
     algo = ALGO_FLOPS_PER_PAIR[wl.filter]
-    peak = peaks_live["fp32_tflops"]
-    peak_src = (f"FP32 FMA throughput measured in this run by the library's probe ({peaks_live['how']}); "
-                f"nominal {FP32_NOMINAL_TFLOPS:.2f} (148 SMs x 128 lanes x 2 x 2032 MHz)")
+    peak, peak_src = fp32_peak(peaks_live)
     roof, per_kernel = kernel_roofline(
         ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, algo, TOEPLITZ_EXEC_FLOPS_PER_PAIR, "k_pixel_toeplitz"),
               "pixel_general": (pairs_gen, algo, GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter], "k_pixel_general"),
@@ -673,9 +681,7 @@ def run_native_galaxy(args, world, rank, peaks_live=None, accuracy_targets=0, pr
     m_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in bin_ms)
     ms_step = max_over_ranks(total, world)
     value = sum_over_ranks(float(pairs_step), world) / (ms_step * 1e-3) / 1e9
-    peak = peaks_live["fp32_tflops"]
-    peak_src = (f"FP32 FMA throughput measured in this run by the library's probe ({peaks_live['how']}); "
-                f"nominal {FP32_NOMINAL_TFLOPS:.2f} (148 SMs x 128 lanes x 2 x 2032 MHz)")
+    peak, peak_src = fp32_peak(peaks_live)
     roof, per_kernel = kernel_roofline(
         ctx, {"galaxy": (pairs_step, ALGO_FLOPS_PER_PAIR[wl.filter], BRUTE_EXEC_FLOPS_PER_PAIR[wl.filter],
                          "k_map_galaxy")}, args.workload, peak, peak_src)

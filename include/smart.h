@@ -399,13 +399,16 @@ smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap
 /*
  * FMA throughput probe (diagnostics; the paper has no counterpart).  Enqueues
  * one kernel of ctas_per_sm (1..8) CTAs of 256 threads per SM on the stream;
- * every thread runs iters x 128 fused multiply-adds in eight independent
- * chains, in float32 (bits = 32) or float64 (bits = 64).  *flops (host)
+ * every thread runs iters x 128 fused multiply-add instructions in eight
+ * independent chains, in float32 (bits = 32), float64 (bits = 64) or on
+ * float32 pairs, two FMAs per packed instruction (bits = 32 |
+ * SMART_PROBE_PACKED; sm_100 and later).  *flops (host)
  * receives the kernel's floating-point operations (an FMA counts 2); the
  * caller times the launch with events on the same stream and divides.
  * Returns at once; SMART_E_ARG for bad arguments, SMART_E_CUDA on a launch
  * failure.  Allocates nothing.
  */
+enum { SMART_PROBE_PACKED = 0x100 };
 smart_status smart_fma_probe(int bits, int64_t iters, int ctas_per_sm, void *cuda_stream, double *flops);
 
 /*

@@ -61,12 +61,16 @@ def pix2vec(nside: int, pix: torch.Tensor) -> torch.Tensor:
     return out
 
 
-def fma_probe(bits: int, iters: int, ctas_per_sm: int = 8, stream=None) -> float:
-    """Enqueue the FMA throughput probe (float32 or float64) on the stream and
-    return its floating-point operation count; time it with events."""
+PROBE_PACKED = 0x100
+
+
+def fma_probe(bits: int, iters: int, ctas_per_sm: int = 8, stream=None, packed: bool = False) -> float:
+    """Enqueue the FMA throughput probe (float32 or float64; packed=True: float32
+    pairs through the packed two-lane instruction) on the stream and return its
+    floating-point operation count; time it with events."""
     flops = ctypes.c_double(0.0)
-    st = N.load().smart_fma_probe(int(bits), int(iters), int(ctas_per_sm), _stream_handle(stream),
-                                  ctypes.byref(flops))
+    st = N.load().smart_fma_probe(int(bits) | (PROBE_PACKED if packed else 0), int(iters), int(ctas_per_sm),
+                                  _stream_handle(stream), ctypes.byref(flops))
     if st:
         raise SmartError(st, "smart_fma_probe")
     return flops.value

@@ -113,3 +113,14 @@ def test_map_calls_return_before_the_work_completes(cuda_device):
     for a, b in zip(busy_maps, quiet_maps):
         for k in a:
             assert torch.equal(a[k], b[k]), k
+
+
+def test_fma_probe_forms(cuda_device):
+    """The probe's three forms run and count their operations: 2 x CTAs x 256
+    threads x iters x 128 FMAs, twice that for the packed float32 pairs."""
+    nsm = torch.cuda.get_device_properties(cuda_device).multi_processor_count
+    base = 2.0 * nsm * 2 * 256 * 64 * 128
+    assert api.fma_probe(32, 64, 2) == base
+    assert api.fma_probe(64, 64, 2) == base
+    assert api.fma_probe(32, 64, 2, packed=True) == 2 * base
+    torch.cuda.synchronize()

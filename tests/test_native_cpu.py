@@ -69,3 +69,9 @@ def test_stateless_calls_reject_bad_arguments():
     assert lib.smart_set_band_slot_limit(None, 1) == 1
     assert lib.smart_last_error(None) == b"null context"
     lib.smart_destroy(None)
+    fl = ctypes.c_double(0.0)
+    for bits in (16, 33, 64 | 0x100, 0x100):            # packed form is float32 only
+        assert lib.smart_fma_probe(bits, 4, 1, None, ctypes.byref(fl)) == 1
+    assert lib.smart_fma_probe(32, 0, 1, None, ctypes.byref(fl)) == 1
+    assert lib.smart_fma_probe(32, 4, 9, None, ctypes.byref(fl)) == 1
+    assert lib.smart_fma_probe(32, 4, 1, None, None) == 1
