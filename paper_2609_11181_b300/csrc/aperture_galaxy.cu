@@ -189,6 +189,7 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
                                             float (&nf)[GT], int (&nn)[GT], int (&nm)[GT]) {
     // a generous pre-filter for the guard band; the exact test follows
     const float Tmid = 0.5f * (a.Tlo + a.Thi), Thw = 0.5f * (a.Thi - a.Tlo) * 1.001f;
+    const float qn1 = a.f.qnorm * a.f.inv_ap2, qn2 = qn1 * a.f.inv_ap2;
     const int n1 = min(len, Rp.nr - lo);
 #pragma unroll 1
     for (int part = 0; part < 2; ++part) {
@@ -208,6 +209,7 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
             float A, B, C, D, frg;
             gal_setup_m<MODE>(R, geo, A, B, C, D, frg);
             const float Gp = (float)krel + frg;          // galaxy on the window's lattice
+            const float g1x2 = 2.0f * sh.x, g2m2 = -2.0f * sh.y;
             float dmin = 3.0e38f;
 #pragma unroll
             for (int r = 0; r < GT; ++r) {
@@ -222,22 +224,30 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
                 const float x = R.mrho0 * sinu;
                 const float y = fmaf(D, h, C);
                 const float xx = x * x;
-                const float sd2 = fmaf(y, y, xx);
                 const float cc = fmaf(y, y, -xx);
-                const float ss = -2.0f * x * y;
-                float Q;
-                if (KIND == SMART_FILTER_POLY && MODE == 0) {
-                    const float X2 = sep2_short(s2) * a.f.inv_ap2;
-                    Q = a.f.qnorm * X2 * (1.0f - X2);
+                const float xy = x * y;
+                // wq = m Q (m: the 0/1 member factor), w = m Q / sin^2 d; the
+                // shear terms take -2xy through the galaxy's (2 g1, -2 g2)
+                float w, wq;
+                if (KIND == SMART_FILTER_POLY) {
+                    // polynomial filter, no division: with t = qnorm/theta^2
+                    // (1 - d^2/theta^2), Q = d^2 t and Q / sin^2 d = t d^2 / sin^2 d
+                    // = t + Q (1/3 + d^2/15 + 2 d^4/189 + ...); MODE 0 (d <= 0.05)
+                    // keeps the first term, the rest is below float32 rounding
+                    const float d2 = MODE == 0 ? sep2_short(s2) : sep2_from_chord2(s2);
+                    const float tm = m * fmaf(d2, -qn2, qn1);
+                    wq = d2 * tm;
+                    const float F = MODE == 0 ? (1.0f / 3.0f)
+                                              : fmaf(d2, fmaf(d2, 2.0f / 189.0f, 1.0f / 15.0f), 1.0f / 3.0f);
+                    w = fmaf(wq, F, tm);
                 } else {
-                    Q = filter_Q<KIND>(a.f, a.f.qtab, s2);
+                    wq = m * filter_Q<KIND>(a.f, a.f.qtab, s2);
+                    // sin^2 d = 0 only for a galaxy at the target's centre, where cc = xy = 0
+                    w = __fdividef(wq, fmaf(y, y, xx) + 1e-30f);
                 }
-                const float wq = m * Q;
-                // sd2 = 0 only for a galaxy at the target's centre, where cc = ss = 0
-                const float w = __fdividef(wq, sd2 + 1e-30f);
-                pe[r] = fmaf(w, fmaf(sh.x, cc, sh.y * ss), pe[r]);
-                pb[r] = fmaf(w, fmaf(sh.y, cc, -sh.x * ss), pb[r]);
-                pv[r] = fmaf(wq * Q, sh.w, pv[r]);
+                pe[r] = fmaf(w, fmaf(sh.x, cc, g2m2 * xy), pe[r]);
+                pb[r] = fmaf(w, fmaf(sh.y, cc, g1x2 * xy), pb[r]);
+                pv[r] = fmaf(wq * wq, sh.w, pv[r]);           // m Q^2 = (m Q)^2
                 pw[r] = fmaf(m, sh.z, pw[r]);
                 if (BARY) {
                     nn[r] += m != 0.f ? cnt : 0;

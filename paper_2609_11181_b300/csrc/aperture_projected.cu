@@ -187,11 +187,21 @@ __device__ __forceinline__ int warp_sum_n(int v) {
 template <int KIND>
 __device__ __forceinline__ void proj_pair(const MapArgs &a, const ProjArgs &p, float dx, float dy, float r2, bool in,
                                           const float4 &sh, float &pe, float &pb, float &pv, float &pw, int &nn) {
-    const float Q = plane_Q<KIND>(a, p, r2);
     const float c2n = fmaf(dx, dx, -dy * dy);        // r^2 cos 2phi
     const float s2n = 2.0f * dx * dy;                // r^2 sin 2phi
-    // r2 = 0 only for a galaxy at the target itself: no shear (c2n = s2n = 0)
-    const float w = in ? __fdividef(Q, r2 + 1e-30f) : 0.f;
+    float Q, w;
+    if (KIND == SMART_FILTER_POLY) {
+        // Q = qnorm X^2 (1 - X^2) with X^2 = r^2 / theta^2, so Q / r^2 =
+        // qnorm/theta^2 (1 - X^2) exactly: no division
+        const float qn1 = a.f.qnorm * a.f.inv_ap2;
+        const float t = fmaf(r2, -qn1 * a.f.inv_ap2, qn1);
+        Q = r2 * t;
+        w = in ? t : 0.f;
+    } else {
+        Q = plane_Q<KIND>(a, p, r2);
+        // r2 = 0 only for a galaxy at the target itself: no shear (c2n = s2n = 0)
+        w = in ? __fdividef(Q, r2 + 1e-30f) : 0.f;
+    }
     pe = fmaf(-w, fmaf(sh.x, c2n, sh.y * s2n), pe);
     pb = fmaf(w, fmaf(sh.x, s2n, -sh.y * c2n), pb);
     pv = fmaf(in ? Q * Q : 0.f, sh.w, pv);
