@@ -298,11 +298,11 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a, cons
         onf[r] = on[r] ? 1.0f : 0.0f;
         j0[r] = on[r] ? (int)(a.targets[tb + r] - ring_start0) : jlast;
     }
-    float SE[GT], cSE[GT], SB[GT], cSB[GT], SV[GT], SW[GT], cSW[GT];
+    float SE[GT], SB[GT], SV[GT], SW[GT];
     int NN[GT], NM[GT];
 #pragma unroll
     for (int r = 0; r < GT; ++r) {
-        SE[r] = cSE[r] = SB[r] = cSB[r] = SV[r] = SW[r] = cSW[r] = 0.f;
+        SE[r] = SB[r] = SV[r] = SW[r] = 0.f;
         NN[r] = NM[r] = 0;
     }
     const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
@@ -356,22 +356,23 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a, cons
         else gal_segment<KIND, 2, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);
 #pragma unroll
         for (int r = 0; r < GT; ++r) {
-            kahan_add(SE[r], cSE[r], pe[r]);
-            kahan_add(SB[r], cSB[r], pb[r]);
+            SE[r] += pe[r];
+            SB[r] += pb[r];
             SV[r] += pv[r];
-            kahan_add(SW[r], cSW[r], pw[r]);
+            SW[r] += pw[r];
             NN[r] += BARY ? nn[r] : (int)nf[r];
             NM[r] += nm[r];
         }
     }
-    // warp reduction of the per-lane sums (compensation folded in first);
+    // warp reduction of the per-lane sums (per lane: float32 partial sums per
+    // ring pair, added to float32 totals);
     // raw sums go to float64 scratch, normalised after the guard-band pairs
 #pragma unroll
     for (int r = 0; r < GT; ++r) {
-        const float se = warp_sum(SE[r] - cSE[r]);
-        const float sb = warp_sum(SB[r] - cSB[r]);
+        const float se = warp_sum(SE[r]);
+        const float sb = warp_sum(SB[r]);
         const float sv = warp_sum(SV[r]);
-        const float sw = warp_sum(SW[r] - cSW[r]);
+        const float sw = warp_sum(SW[r]);
         const int n = warp_sum_i(NN[r]);
         const int m = BARY ? warp_sum_i(NM[r]) : 0;
         if (lane == r && on[r]) {

@@ -230,11 +230,11 @@ __global__ void __launch_bounds__(32 * PW, 2) k_map_projected(const MapArgs a, c
         if (!on[r]) T[r] = make_float4(-1e18f, -1e18f, 0.f, 0.f);
         j0[r] = r < nt ? (int)(a.targets[tb + r] - ring_start0) : tr0.j0;
     }
-    float SE[PT], cSE[PT], SB[PT], cSB[PT], SV[PT], SW[PT], cSW[PT];
+    float SE[PT], SB[PT], SV[PT], SW[PT];
     int NN[PT];
 #pragma unroll
     for (int r = 0; r < PT; ++r) {
-        SE[r] = cSE[r] = SB[r] = cSB[r] = SV[r] = SW[r] = cSW[r] = 0.f;
+        SE[r] = SB[r] = SV[r] = SW[r] = 0.f;
         NN[r] = 0;
     }
     const int64_t row0 = (int64_t)(tr0.i0 - 1) * a.kmax;
@@ -312,19 +312,19 @@ __global__ void __launch_bounds__(32 * PW, 2) k_map_projected(const MapArgs a, c
         }
 #pragma unroll
         for (int r = 0; r < PT; ++r) {
-            kahan_add(SE[r], cSE[r], pe[r]);
-            kahan_add(SB[r], cSB[r], pb[r]);
+            SE[r] += pe[r];
+            SB[r] += pb[r];
             SV[r] += pv[r];
-            kahan_add(SW[r], cSW[r], pw[r]);
+            SW[r] += pw[r];
             NN[r] += nn[r];
         }
     }
 #pragma unroll
     for (int r = 0; r < PT; ++r) {
-        const float se = warp_sum_f(SE[r] - cSE[r]);
-        const float sb = warp_sum_f(SB[r] - cSB[r]);
+        const float se = warp_sum_f(SE[r]);
+        const float sb = warp_sum_f(SB[r]);
         const float sv = warp_sum_f(SV[r]);
-        const float sw = warp_sum_f(SW[r] - cSW[r]);
+        const float sw = warp_sum_f(SW[r]);
         const int n = warp_sum_n(NN[r]);
         if (lane == r && r < nt) {
             double *raw = a.raw + 4 * (tb + r);
