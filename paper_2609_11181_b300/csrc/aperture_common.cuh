@@ -99,6 +99,16 @@ __device__ __forceinline__ float qtab_eval(const float4 *tab, float s2, float sc
     return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
 }
 
+// the same for a member pair (s2 below T, so the index stays below
+// QTAB_BINS: no clamp)
+__device__ __forceinline__ float qtab_eval_member(const float4 *tab, float s2, float scale) {
+    const float f = sqrt_approx(s2) * scale;
+    const int i = (int)f;
+    const float t = f - (float)i;
+    const float4 c = tab[i];
+    return fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+}
+
 // Q(d) from the chord^2.  Polynomial filter in closed form; the tabulated
 // filters (Schirmer, Jarvis) through their cubic table (tab: a shared-memory
 // or global copy).  KIND == SMART_FILTER_SCHIRMER stands for every tabulated

@@ -179,8 +179,8 @@ __device__ __forceinline__ float sep2_short(float s2) { return s2 * fmaf(s2, 1.0
 // through a 0/1 factor); a galaxy whose chord^2 to any target lies inside the
 // guard band takes one rare branch to the float64 list.  Targets past the
 // group's end sit far away (never members).  MODE picks the series: 0 when
-// every |u| and |dl| of the ring pair stays below 0.05 rad, 1 below 0.45,
-// 2 beyond.
+// every |u| and |dl| of the ring pair stays below 0.05 rad and theta_ap
+// below 0.03 rad, 1 when they stay below 0.45, 2 beyond.
 template <int KIND, int MODE, bool BARY>
 __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba, const RingPair &Rp, const GalRing &R,
                                             int e, int lane, int64_t tb, const float (&Tr)[GT],
@@ -232,8 +232,9 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
                 if (KIND == SMART_FILTER_POLY) {
                     // polynomial filter, no division: with t = qnorm/theta^2
                     // (1 - d^2/theta^2), Q = d^2 t and Q / sin^2 d = t d^2 / sin^2 d
-                    // = t + Q (1/3 + d^2/15 + 2 d^4/189 + ...); MODE 0 (d <= 0.05)
-                    // keeps the first term, the rest is below float32 rounding
+                    // = t + Q (1/3 + d^2/15 + 2 d^4/189 + ...); MODE 0 (members
+                    // within theta_ap <= 0.03) keeps the first term, the rest
+                    // lies below float32 rounding
                     const float d2 = MODE == 0 ? sep2_short(s2) : sep2_from_chord2(s2);
                     const float tm = m * fmaf(d2, -qn2, qn1);
                     wq = d2 * tm;
@@ -349,8 +350,11 @@ __global__ void __launch_bounds__(32 * GW, 2) k_map_galaxy(const MapArgs a, cons
         const int len = uhi - ulo + 1;
         // series by the largest |u| (window plus one pixel) and |dl| (ring
         // offset plus a bin pixel's half extent) of the ring pair
+        // (MODE 0 also needs theta_ap <= 0.03 rad: its polynomial-filter weight
+        // keeps one term of the d^2 / sin^2 d series, d^4/15 < 6e-8 beyond)
         const int mode = (Rp.flags & RP_WIDE) ? 2
-                         : ((float)(len + 2) * Rp.dphi <= 0.05f && fabsf(Rp.dlat) + a.pixrad <= 0.05f) ? 0 : 1;
+                         : ((float)(len + 2) * Rp.dphi <= 0.05f && fabsf(Rp.dlat) + a.pixrad <= 0.05f &&
+                            a.T <= 9e-4) ? 0 : 1;
         if (mode == 0) gal_segment<KIND, 0, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);
         else if (mode == 1) gal_segment<KIND, 1, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);
         else gal_segment<KIND, 2, BARY>(a, ba, Rp, R, e, lane, tb, Tr, onf, lo, len, pe, pb, pv, pw, nf, nn, nm);

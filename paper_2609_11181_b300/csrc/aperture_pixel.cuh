@@ -125,44 +125,66 @@ __device__ __forceinline__ int wrap_start(const RingPair &R, int Xi, int k) {
     return kk;
 }
 
+// One member pair of the general path: bin pixel data g at lattice offset
+// kf.  u from the offset each time (not by repeated addition): the
+// target's own pixel must get u = 0 exactly, so that it carries no shear.
+// Tabulated filters: the table index needs no clamp (a member's chord is
+// below the aperture's).  Polynomial filter: Q / sin^2 d without a
+// division, t + Q (1/3 + d^2/15 + 2 d^4/189) with t = qnorm/theta^2 (1 -
+// d^2/theta^2) and Q = d^2 t (truncation below 2e-10 relative for chords
+// up to 0.22, which the polynomial's series for d^2 needs anyway).
+template <int KIND, int MODE>
+__device__ __forceinline__ void member_pair(const MapArgs &a, const RingPair &R, const float4 *qtab, float u0,
+                                            float kf, const float4 &g, float &pe, float &pb, float &pv, float &pw) {
+    const float u = fmaf(kf, R.dphi, u0);
+    float sinu, h;
+    sin_hav<MODE>(u, sinu, h);
+    const float s2 = fmaf(R.B, h, R.A);
+    const float x = R.mrho0 * sinu;
+    const float y = fmaf(R.D, h, R.C);
+    const float xx = x * x;
+    const float cc = fmaf(y, y, -xx);
+    const float ss = -2.0f * x * y;
+    float Q, w;
+    if (KIND == SMART_FILTER_POLY) {
+        const float d2 = sep2_from_chord2(s2);
+        const float qn1 = a.f.qnorm * a.f.inv_ap2;
+        const float t = fmaf(d2, -qn1 * a.f.inv_ap2, qn1);
+        Q = d2 * t;
+        w = fmaf(Q, fmaf(d2, fmaf(d2, 2.0f / 189.0f, 1.0f / 15.0f), 1.0f / 3.0f), t);
+    } else {
+        Q = qtab_eval_member(qtab, s2, a.f.tab_scale);
+        // sin^2 d = 0 only at the target's own centre, where cc = ss = 0
+        // exactly; elsewhere it is at least a squared bin spacing, far above
+        // the offset, which only keeps w finite there
+        w = __fdividef(Q, fmaf(y, y, xx) + 1e-30f);
+    }
+    pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
+    pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
+    pv = fmaf(Q * Q, g.z, pv);
+    pw += g.w;
+}
+
 // The certain members of one ring pair that do not cross the bin ring's
-// seam: bin pixels pbeg .. pbeg + cnt - 1 at lattice offsets kf, kf + 1, ...
-// No test, no select: every pair is a member.  The bin pixel's data is loaded
-// one iteration ahead (the last load repeats, never past the run).
+// seam: bin pixels pbeg .. pbeg + cnt - 1 (cnt >= 1) at lattice offsets kf,
+// kf + 1, ...  No test, no select: every pair is a member.  The bin pixel's
+// data is loaded one iteration ahead; the last pair is peeled off the loop
+// so that no load passes the run.
 template <int KIND, int MODE>
 __device__ __forceinline__ void certain_run(const MapArgs &a, const RingPair &R, const float4 *qtab, float u0,
                                             float kf, int pbeg, int cnt, float &pe, float &pb, float &pv,
                                             float &pw) {
     const float4 *pp = a.PX + pbeg;
     float4 gn = __ldg(pp);
+    const int last = cnt - 1;
 #pragma unroll 2
-    for (int i = 0; i < cnt; ++i) {
+    for (int i = 0; i < last; ++i) {
         const float4 g = gn;
-        gn = __ldg(pp + min(i + 1, cnt - 1));
-        // u from the offset each time (not by repeated addition): the
-        // target's own pixel must get u = 0 exactly, so that it carries no
-        // shear
-        const float u = fmaf(kf, R.dphi, u0);
+        gn = __ldg(pp + i + 1);
+        member_pair<KIND, MODE>(a, R, qtab, u0, kf, g, pe, pb, pv, pw);
         kf += 1.0f;
-        float sinu, h;
-        sin_hav<MODE>(u, sinu, h);
-        const float s2 = fmaf(R.B, h, R.A);
-        const float x = R.mrho0 * sinu;
-        const float y = fmaf(R.D, h, R.C);
-        const float xx = x * x;
-        const float sd2 = fmaf(y, y, xx);
-        const float cc = fmaf(y, y, -xx);
-        const float ss = -2.0f * x * y;
-        const float Q = filter_Q<KIND>(a.f, qtab, s2);
-        // sd2 = 0 only at the target's own centre, where cc = ss = 0
-        // exactly; elsewhere sd2 is at least a squared bin spacing, far
-        // above the offset, which only keeps w finite there
-        const float w = __fdividef(Q, sd2 + 1e-30f);
-        pe = fmaf(w, fmaf(g.x, cc, g.y * ss), pe);
-        pb = fmaf(w, fmaf(g.y, cc, -g.x * ss), pb);
-        pv = fmaf(Q * Q, g.z, pv);
-        pw += g.w;
     }
+    member_pair<KIND, MODE>(a, R, qtab, u0, kf, gn, pe, pb, pv, pw);
 }
 
 // pixel-mode general pair loop for one target and one ring pair; MODE picks
