@@ -453,8 +453,8 @@ def run_native_pixel(args, world, rank):
     # (smart_set_binned_runs; outside the footprint the binned data are zero,
     # so the maps equal the device run's bit for bit); the results read back
     # are the maps of the method, M_E, M_B and sigma^2 (the weight sums stay
-    # on the device: host<->device copies share the link, about 75 GB/s both
-    # ways together on this machine, so every byte counts).  Steps are pipelined the way
+    # on the device: copies in the two directions share the host link's
+    # bandwidth).  Steps are pipelined the way
     # a serving loop would run them: double-buffered device inputs and
     # outputs, host->device copies on one stream, the map on the context's
     # stream, device->host copies on a third, so step k + 1's copy in and
