@@ -454,11 +454,12 @@ def run_native_pixel(args, world, rank):
     # so the maps equal the device run's bit for bit); the results read back
     # are the maps of the method, M_E, M_B and sigma^2 (the weight sums stay
     # on the device: copies in the two directions share the host link's
-    # bandwidth).  Steps are pipelined the way
-    # a serving loop would run them: double-buffered device inputs and
-    # outputs, host->device copies on one stream, the map on the context's
-    # stream, device->host copies on a third, so step k + 1's copy in and
-    # step k - 1's copy out overlap step k's map.
+    # bandwidth).  Steps are pipelined the way a serving loop would run them:
+    # double-buffered device inputs and outputs, host->device copies on one
+    # stream, the map on the context's stream, device->host copies on a
+    # third.  An input buffer is free again as soon as smart_set_binned_runs
+    # has copied it into the context's map, so step k + 1's copy in and step
+    # k - 1's copy out overlap step k's map.
     foot = wl.targets.cpu().numpy()                  # the footprint's pixels (where the data are)
     brk = np.nonzero(np.diff(foot) != 1)[0] + 1
     r_first = np.concatenate([[0], brk])
@@ -477,8 +478,9 @@ def run_native_pixel(args, world, rank):
     outs = [ectx._out(None)[0] for _ in range(2)]
     host_out = [{k: torch.empty(out[k].shape, dtype=out[k].dtype, pin_memory=True) for k in read_back}
                 for _ in range(2)]
-    e_steps = max(4, min(args.steps, 8))
+    e_steps = max(8, min(2 * args.steps, 16))          # a pipeline: fill and drain are paid once
     ev_in = [torch.cuda.Event() for _ in range(e_steps)]
+    ev_set = [torch.cuda.Event() for _ in range(e_steps)]
     ev_map = [torch.cuda.Event() for _ in range(e_steps)]
     ev_out = [torch.cuda.Event() for _ in range(e_steps)]
 
@@ -486,7 +488,9 @@ def run_native_pixel(args, world, rank):
         for k in range(n):
             i = k % 2
             if k >= 2:
-                s_in.wait_event(ev_map[k - 2])        # inputs of buffer i no longer read
+                # inputs of buffer i no longer read: smart_set_binned_runs has
+                # copied them into the context's map
+                s_in.wait_event(ev_set[k - 2])
             with torch.cuda.stream(s_in):
                 for d, h in zip(dev_in[i], host_in):
                     d.copy_(h, non_blocking=True)
@@ -495,6 +499,7 @@ def run_native_pixel(args, world, rank):
             if k >= 2:
                 s_map.wait_event(ev_out[k - 2])       # outputs of buffer i read back
             ectx.set_binned_runs(*dev_in[i])
+            ev_set[k].record(s_map)
             ectx.map_pixel(outs[i])
             ev_map[k].record(s_map)
             s_out.wait_event(ev_map[k])
