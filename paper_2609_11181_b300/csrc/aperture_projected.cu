@@ -116,6 +116,25 @@ __global__ void k_plane_setup(double ra_c, double dec_c, double *out) {
     out[8] = cd;
 }
 
+// The records only need their positions to about 2^-48 (the float32 hi/lo
+// pairs) and the shear rotation to float32: the float64 membership
+// decisions recompute positions in the reference's order of operations
+// (plane_xy64), so the records take cheaper steps -- the quadrant of an
+// angle from a product with 1/90 instead of a division (the reduced angle
+// may pass 45 degrees by an ulp, where the series is as accurate), one
+// reciprocal for both plane coordinates, and the rotation in float32.
+__device__ __forceinline__ void sincos_deg64_rec(double x, double &s, double &c) {
+    const double q = rint(__dmul_rn(x, 1.0 / 90.0));
+    const double y = __dadd_rn(x, -__dmul_rn(q, 90.0));
+    double ss, cc;
+    series_sincos(__dmul_rn(y, SMART_PI / 180.0), ss, cc);
+    const int k = (int)((long long)q & 3);
+    if (k == 0) { s = ss; c = cc; }
+    else if (k == 1) { s = cc; c = -ss; }
+    else if (k == 2) { s = -ss; c = -cc; }
+    else { s = -cc; c = ss; }
+}
+
 // step 1: plane position and rotated shear of every sorted galaxy
 __global__ void k_proj_records(int64_t n, const double2 *__restrict__ radec, const float4 *__restrict__ sh_in,
                                const double *__restrict__ plane, float4 *__restrict__ gxy, float4 *__restrict__ gsh) {
@@ -123,28 +142,31 @@ __global__ void k_proj_records(int64_t n, const double2 *__restrict__ radec, con
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const double2 rd = radec[k];
         double sa, ca, sd, cd;
-        sincos_deg64(rd.x, sa, ca);
-        sincos_deg64(rd.y, sd, cd);
-        const double rx = __dmul_rn(cd, ca), ry = __dmul_rn(cd, sa), rz = sd;
-        double x, y, X, Y, D;
-        if (!plane_xy64(P, rx, ry, rz, x, y, &X, &Y, &D)) {
+        sincos_deg64_rec(rd.x, sa, ca);
+        sincos_deg64_rec(rd.y, sd, cd);
+        const double rx = cd * ca, ry = cd * sa, rz = sd;
+        const double D = rx * P.c[0] + ry * P.c[1] + rz * P.c[2];
+        if (!(D > 0.0)) {
             // no image: far outside every aperture, never a member (finite,
             // so that every product of the pair body stays finite)
             gxy[k] = make_float4(1e18f, 1e18f, 0.f, 0.f);
             gsh[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             continue;
         }
-        gxy[k] = split_xy(x, y);
+        const double X = rx * P.e[0] + ry * P.e[1] + rz * P.e[2];
+        const double Y = rx * P.n[0] + ry * P.n[1] + rz * P.n[2];
+        const double iD = 1.0 / D;
+        gxy[k] = split_xy(X * iD, Y * iD);
         // image of the local North t = (-sin d cos a, -sin d sin a, cos d),
         // up to the positive factor 1 / D^2
         const double tx = -sd * ca, ty = -sd * sa, tz = cd;
         const double tc = tx * P.c[0] + ty * P.c[1] + tz * P.c[2];
         const double te = tx * P.e[0] + ty * P.e[1] + tz * P.e[2];
         const double tn = tx * P.n[0] + ty * P.n[1] + tz * P.n[2];
-        const double Nx = te * D - X * tc, Ny = tn * D - Y * tc;
-        const double nn = Nx * Nx + Ny * Ny;
-        const float c2 = (float)((Ny * Ny - Nx * Nx) / nn);      // cos 2 rho
-        const float s2 = (float)(-2.0 * Nx * Ny / nn);           // sin 2 rho
+        const float Nx = (float)(te * D - X * tc), Ny = (float)(tn * D - Y * tc);
+        const float inn = 1.0f / fmaf(Nx, Nx, Ny * Ny);
+        const float c2 = (Ny * Ny - Nx * Nx) * inn;              // cos 2 rho
+        const float s2 = -2.0f * Nx * Ny * inn;                  // sin 2 rho
         const float4 g = sh_in[k];                                // (w e1, w e2, w, w^2 |e|^2)
         gsh[k] = make_float4(g.x * c2 - g.y * s2, g.x * s2 + g.y * c2, g.z, g.w);
     }
