@@ -59,11 +59,13 @@ ALGO_FLOPS_PER_PAIR = {"poly": 45, "schirmer": 54, "jarvis": 54}
 # one add for the weight.
 TOEPLITZ_EXEC_FLOPS_PER_PAIR = 11
 # Executed float32 work per pair of the general pixel kernel, counted from its
-# pair body (FMA = 2): lattice offset 2, sine / haversine series 15, chord 2,
-# tangent-plane direction and cos / sin 2psi 10, filter 15 (Schirmer table) or
-# 9 + 3 (chord-to-separation series + polynomial), weight 1, E / B 10, variance
-# and weight sums 4.
-GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 68, "jarvis": 68, "poly": 56}
+# pair body for the two-term series (FMA = 2, a hardware square root or
+# reciprocal = 1): lattice offset 3, sine / haversine series 7, chord 2,
+# tangent-plane direction and cos / sin 2psi 10, E / B 10, variance and weight
+# sums 4; tabulated filter 9 (table coordinate, cubic) + weight 5 (sin^2 d,
+# reciprocal); polynomial 18 (chord-to-separation series, Q and Q / sin^2 d
+# without a division).
+GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 48, "jarvis": 48, "poly": 52}
 
 
 def _env_int(k, d):
@@ -258,14 +260,15 @@ def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_
     """Roofline of the dominant kernel from the context's per-launch events.
 
     kernels: {name: (pairs per launch, algorithmic flops per pair, executed
-    flops per pair, kernel symbol)}.  The dominant kernel is the one with the
-    largest summed time over the timed steps; achieved = algorithmic flops per
-    launch (the direct-form count per pair x member pairs) / its mean launch
-    time, or the executed flops where they are fewer (a kernel that shares
-    work between pairs, the Toeplitz kernel, is held to what it executes).
-    Both are reported per kernel."""
+    flops per pair, kernel symbol, shares work between pairs)}.  The dominant
+    kernel is the one with the largest summed time over the timed steps;
+    achieved = algorithmic flops per launch (the direct-form count per pair x
+    member pairs) / its mean launch time, except for a kernel that shares work
+    between pairs (the Toeplitz kernel: one geometry entry serves every target
+    at the same ring offset), which is held to the flops it executes.  Both
+    figures are reported per kernel."""
     per = {}
-    for name, (pairs, fpp, exec_fpp, sym) in kernels.items():
+    for name, (pairs, fpp, exec_fpp, sym, shares) in kernels.items():
         n, ms = ctx.timing_read(name)
         if n == 0:
             continue
@@ -273,16 +276,16 @@ def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_
         per[name] = {"kernel": sym, "launches": n, "total_ms": round(ms, 3), "ms_per_launch": round(ms / n, 4),
                      "pairs_per_launch": int(pairs), "gpair_s": round(pairs / t / 1e9, 2) if t > 0 else None,
                      "algorithmic_flops_per_pair": fpp, "executed_flops_per_pair": exec_fpp,
+                     "shares_work_between_pairs": shares,
                      "algorithmic_tflops": round(pairs * fpp / t / 1e12, 2) if t > 0 and fpp else None,
                      "executed_tflops": round(pairs * exec_fpp / t / 1e12, 2) if t > 0 and exec_fpp else None}
     if not per:
         return None, per
     dom = max(per, key=lambda k: per[k]["total_ms"])
     d = per[dom]
-    if d["executed_flops_per_pair"] is None or d["algorithmic_flops_per_pair"] <= d["executed_flops_per_pair"]:
-        achieved, basis = d["algorithmic_tflops"], "algorithmic flops (direct form per pair)"
+    if not d["shares_work_between_pairs"]:
+        achieved, basis = d["algorithmic_tflops"], "algorithmic flops (direct form per member pair)"
     else:
-        # a kernel that shares work between pairs is held to what it executes
         achieved, basis = d["executed_tflops"], "executed flops (work shared between pairs)"
     roof = {"bound": "alu", "achieved": achieved, "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
             "frac": round(achieved / peak_tflops, 4), "traffic": profiled_traffic(d["kernel"], workload),
@@ -436,9 +439,9 @@ def run_native_pixel(args, world, rank):
     algo = ALGO_FLOPS_PER_PAIR[wl.filter]
     peak, peak_src = fp32_peak(peaks_live)
     roof, per_kernel = kernel_roofline(
-        ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, algo, TOEPLITZ_EXEC_FLOPS_PER_PAIR, "k_pixel_toeplitz"),
-              "pixel_general": (pairs_gen, algo, GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter], "k_pixel_general"),
-              "pixel_band": (0, None, None, "k_pixel_band")},
+        ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, algo, TOEPLITZ_EXEC_FLOPS_PER_PAIR, "k_pixel_toeplitz", True),
+              "pixel_general": (pairs_gen, algo, GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter], "k_pixel_general", False),
+              "pixel_band": (0, None, None, "k_pixel_band", False)},
         args.workload, peak, peak_src)
     ctx.timing(False)
     npix_bin = 12 * wl.nside ** 2
@@ -566,10 +569,14 @@ def run_native_pixel(args, world, rank):
 
 
 GALAXY_WORKLOADS = workloads.GALAXY_WORKLOADS
-# executed float32 flops per member pair of the brute-force kernel (source
-# count, FMA = 2): offsets 2, latitude series 10, azimuth series 9, chord 3,
-# direction + 2psi 10, filter 8, weight 1, E/B 10, variance + weight 4
-BRUTE_EXEC_FLOPS_PER_PAIR = {"poly": 57, "schirmer": 62, "jarvis": 62}
+# executed float32 flops per evaluated pair of the brute-force kernel (source
+# count for the two-term series, FMA = 2): offsets 2, azimuth series 7, chord
+# 2, band distance 1, direction + 2psi 7, E/B 10, variance + weight + count 6,
+# polynomial filter and Q / sin^2 d 9 (tabulated: 15), plus the galaxy's
+# latitude series and set-up (14) shared by the warp's four targets (3.5);
+# every galaxy of the union of the four windows is evaluated (about 1.4 pairs
+# per member pair)
+BRUTE_EXEC_FLOPS_PER_PAIR = {"poly": 48, "schirmer": 54, "jarvis": 54}
 
 
 def projected_leg(ctx, wl, cat, out_sph, steps, accuracy_targets):
@@ -691,7 +698,7 @@ def run_native_galaxy(args, world, rank, peaks_live=None, accuracy_targets=0, pr
     peak, peak_src = fp32_peak(peaks_live)
     roof, per_kernel = kernel_roofline(
         ctx, {"galaxy": (pairs_step, ALGO_FLOPS_PER_PAIR[wl.filter], BRUTE_EXEC_FLOPS_PER_PAIR[wl.filter],
-                         "k_map_galaxy")}, args.workload, peak, peak_src)
+                         "k_map_galaxy", False)}, args.workload, peak, peak_src)
     phases = {}
     for name in ("bin_keys", "bin_sort", "bin_records", "bin_pixel_sums", "galaxy_band", "galaxy_finalise"):
         nl, ms = ctx.timing_read(name)
