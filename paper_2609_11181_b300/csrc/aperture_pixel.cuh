@@ -177,7 +177,7 @@ __device__ __forceinline__ void certain_run(const MapArgs &a, const RingPair &R,
     const float4 *pp = a.PX + pbeg;
     float4 gn = __ldg(pp);
     const int last = cnt - 1;
-#pragma unroll 2
+#pragma unroll 4
     for (int i = 0; i < last; ++i) {
         const float4 g = gn;
         gn = __ldg(pp + i + 1);
