@@ -58,14 +58,14 @@ ALGO_FLOPS_PER_PAIR = {"poly": 45, "schirmer": 54, "jarvis": 54}
 # every target, so a pair costs 4 FMAs for E and B, 1 FMA for the variance and
 # one add for the weight.
 TOEPLITZ_EXEC_FLOPS_PER_PAIR = 11
-# Executed float32 work per pair of the general pixel kernel, counted from its
-# pair body for the two-term series (FMA = 2, a hardware square root or
-# reciprocal = 1): lattice offset 3, sine / haversine series 7, chord 2,
-# tangent-plane direction and cos / sin 2psi 10, E / B 10, variance and weight
-# sums 4; tabulated filter 9 (table coordinate, cubic) + weight 5 (sin^2 d,
-# reciprocal); polynomial 18 (chord-to-separation series, Q and Q / sin^2 d
-# without a division).
-GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 48, "jarvis": 48, "poly": 52}
+# Executed float32 work per pair of the general pixel kernel: 49 measured with
+# a tabulated filter (ncu: fadd + fmul + 2 ffma thread instructions per pair,
+# NSIDE 2048 case), matching the pair body's count (FMA = 2, a hardware square
+# root or reciprocal = 1): lattice offset 3, sine / haversine series 7, chord
+# 2, tangent-plane direction and cos / sin 2psi 10, E / B 10, variance and
+# weight sums 4, table 9, weight 5; the polynomial filter replaces table and
+# weight (14) by the chord-to-separation series, Q and Q / sin^2 d (18).
+GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 49, "jarvis": 49, "poly": 53}
 
 
 def _env_int(k, d):
@@ -569,14 +569,14 @@ def run_native_pixel(args, world, rank):
 
 
 GALAXY_WORKLOADS = workloads.GALAXY_WORKLOADS
-# executed float32 flops per evaluated pair of the brute-force kernel (source
-# count for the two-term series, FMA = 2): offsets 2, azimuth series 7, chord
-# 2, band distance 1, direction + 2psi 7, E/B 10, variance + weight + count 6,
-# polynomial filter and Q / sin^2 d 9 (tabulated: 15), plus the galaxy's
-# latitude series and set-up (14) shared by the warp's four targets (3.5);
-# every galaxy of the union of the four windows is evaluated (about 1.4 pairs
-# per member pair)
-BRUTE_EXEC_FLOPS_PER_PAIR = {"poly": 48, "schirmer": 54, "jarvis": 54}
+# executed float32 flops per member pair of the brute-force kernel: 75
+# measured for the polynomial filter (ncu: fadd + fmul + 2 ffma thread
+# instructions per member pair, 4e6-galaxy case): every galaxy of the union of
+# the four targets' windows is evaluated for all four (about 1.4 pairs per
+# member pair), plus each galaxy's set-up; a tabulated filter adds about 6 per
+# evaluated pair (table lookup and a division instead of the polynomial's
+# division-free weight)
+BRUTE_EXEC_FLOPS_PER_PAIR = {"poly": 75, "schirmer": 83, "jarvis": 83}
 
 
 def projected_leg(ctx, wl, cat, out_sph, steps, accuracy_targets):
