@@ -30,11 +30,11 @@ struct BatchItem {
 };
 
 // the Toeplitz tiles of every map, claimed longest first by resident CTAs
-template <int KIND>
-__global__ void __launch_bounds__(NT, TOE_CTAS_PER_SM) k_pixel_batched(const MapArgs *__restrict__ maps,
+template <int KIND, int NC>
+__global__ void __launch_bounds__(NT, toe_ctas_per_sm<NC>()) k_pixel_batched(const MapArgs *__restrict__ maps,
                                                           const BatchItem *__restrict__ items, int64_t n_items,
                                                           int *__restrict__ work) {
-    __shared__ __align__(16) ToeShared S;
+    __shared__ __align__(16) ToeShared<NC> S;
     __shared__ int s_item;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(NT, TOE_CTAS_PER_SM) k_pixel_batched(const Map
         __syncthreads();   // every thread has read s_item
         if (item >= n_items) break;
         const BatchItem it = items[item];
-        toeplitz_tile<KIND>(maps[it.map], it.index, S);
+        toeplitz_tile<KIND, NC>(maps[it.map], it.index, S);
     }
 }
 
@@ -113,7 +113,8 @@ struct smart_batch {
     cudaGraphExec_t exec = nullptr;
     bool own_stream = false;
     int kind = 0;
-    int ctas_per_sm = TOE_CTAS_PER_SM;
+    bool short_runs = true;   // every map's Toeplitz runs fit the smaller staging
+    int ctas_per_sm = toe_ctas_per_sm<NCAND_SHORT>();
     int order = 0;            // 0: longest first, 1: natural
     double tuned_ms = 0.0;
     std::string err;
@@ -166,10 +167,22 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
     if (b->n_items > 0) {
         const unsigned grid = (unsigned)std::min<int64_t>(b->n_items, (int64_t)sms * ctas_per_sm);
         const BatchItem *items = b->d_items + (order == 0 ? 0 : b->n_items);
-        if (b->kind == SMART_FILTER_POLY)
-            k_pixel_batched<SMART_FILTER_POLY><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
-        else
-            k_pixel_batched<SMART_FILTER_SCHIRMER><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items, b->d_work);
+        const bool poly = b->kind == SMART_FILTER_POLY;
+        if (b->short_runs) {
+            if (poly)
+                k_pixel_batched<SMART_FILTER_POLY, NCAND_SHORT><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items,
+                                                                                           b->d_work);
+            else
+                k_pixel_batched<SMART_FILTER_SCHIRMER, NCAND_SHORT><<<grid, NT, 0, b->stream>>>(b->d_maps, items,
+                                                                                               b->n_items, b->d_work);
+        } else {
+            if (poly)
+                k_pixel_batched<SMART_FILTER_POLY, NCAND><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items,
+                                                                                     b->d_work);
+            else
+                k_pixel_batched<SMART_FILTER_SCHIRMER, NCAND><<<grid, NT, 0, b->stream>>>(b->d_maps, items, b->n_items,
+                                                                                         b->d_work);
+        }
     }
     if (fork) {
         if (cudaEventRecord(b->ev_join, b->side) != cudaSuccess ||
@@ -266,6 +279,10 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
         a.work = nullptr;
         a.fp64_count = c->d_fp64_count;
         b->args[m] = a;
+        if (c->toe_max_run > NCAND_SHORT) {
+            b->short_runs = false;
+            b->ctas_per_sm = toe_ctas_per_sm<NCAND>();
+        }
         // the per-pair cost grows with the number of pixels in an aperture
         const double pix_per_ap = 3.0 * c->nside_bin * c->nside_bin / SMART_PI * c->area;
         if (a.n > 0 && a.n_gen < a.n) {
@@ -346,8 +363,9 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         double best = 1e30;
-        // resident one-warp CTAs per SM: the shared-memory limit, and fewer
-        const int shapes[] = {TOE_CTAS_PER_SM - 4, TOE_CTAS_PER_SM - 2, TOE_CTAS_PER_SM};
+        // resident one-warp CTAs per SM: the register or shared-memory limit, and fewer
+        const int cmax = b->short_runs ? toe_ctas_per_sm<NCAND_SHORT>() : toe_ctas_per_sm<NCAND>();
+        const int shapes[] = {cmax - 4, cmax - 2, cmax};
         for (int order = 0; order < 2 && st == SMART_OK; ++order) {
             for (int cps : shapes) {
                 st = batch_launch(b, cps, order);       // warm

@@ -55,7 +55,7 @@ __device__ __forceinline__ void output_ring_shape(int64_t N0, int64_t i0, int &n
     }
 }
 
-__global__ void k_toe_count(const MapArgs a, int64_t nring, int32_t *__restrict__ cnt) {
+__global__ void k_toe_count(const MapArgs a, int64_t nring, int32_t *__restrict__ cnt, int32_t *__restrict__ cmax) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= nring * a.kmax) return;
     const int64_t i0 = 1 + idx / a.kmax;
@@ -68,6 +68,7 @@ __global__ void k_toe_count(const MapArgs a, int64_t nring, int32_t *__restrict_
         if (toe_candidates(a.N0, a.N1, a.table[idx], nr0, s0, dlo, ncand, fr0)) c = ncand;
     }
     cnt[idx] = c;
+    if (c > 0) atomicMax(cmax, c);
 }
 
 template <int KIND>
@@ -146,9 +147,9 @@ __global__ void k_toe_fill(const MapArgs a, int64_t nring, const int32_t *__rest
 // Toeplitz kernel: persistent CTAs over the tile list; tiles of other
 // output rings are skipped (the general kernel has them).
 // ------------------------------------------------------------------------
-template <int KIND>
-__global__ void __launch_bounds__(NT, TOE_CTAS_PER_SM) k_pixel_toeplitz(const MapArgs a) {
-    __shared__ __align__(16) ToeShared S;
+template <int KIND, int NC>
+__global__ void __launch_bounds__(NT, toe_ctas_per_sm<NC>()) k_pixel_toeplitz(const MapArgs a) {
+    __shared__ __align__(16) ToeShared<NC> S;
     __shared__ int s_tile;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(a.work, 1);
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(NT, TOE_CTAS_PER_SM) k_pixel_toeplitz(const Ma
         if (tile >= a.n_tiles) break;
         const bool want = toeplitz_tile_wanted(a, tile);
         __syncthreads();   // s_tile is read by every thread before it is rewritten
-        if (want) toeplitz_tile<KIND>(a, tile, S);
+        if (want) toeplitz_tile<KIND, NC>(a, tile, S);
     }
 }
 
@@ -360,18 +361,22 @@ smart_status ensure_filter_table(smart_ctx *c) { return build_filter_table(c, fa
 static smart_status build_toeplitz(smart_ctx *c, const MapArgs &a) {
     const int64_t nring = 4 * (int64_t)c->nside_out - 1;
     const int64_t nidx = nring * a.kmax;
-    int32_t *cnt = nullptr, *off = nullptr;
-    if (cudaMallocAsync(&cnt, (size_t)(2 * nidx + 1) * sizeof(int32_t), c->stream) != cudaSuccess)
+    int32_t *cnt = nullptr, *off = nullptr, *cmax = nullptr;
+    if (cudaMallocAsync(&cnt, (size_t)(2 * nidx + 2) * sizeof(int32_t), c->stream) != cudaSuccess)
         return fail(c, SMART_E_NOMEM, "cudaMallocAsync(toeplitz counts) failed");
     off = cnt + nidx;
-    k_toe_count<<<(unsigned)((nidx + 255) / 256), 256, 0, c->stream>>>(a, nring, cnt);
+    cmax = off + nidx + 1;
+    cudaMemsetAsync(cmax, 0, sizeof(int32_t), c->stream);
+    k_toe_count<<<(unsigned)((nidx + 255) / 256), 256, 0, c->stream>>>(a, nring, cnt, cmax);
     smart_status st = exclusive_scan_i32(c, cnt, off, nidx, nidx + 1);
     int32_t total = 0;
     if (st == SMART_OK) {
         int32_t *h = reinterpret_cast<int32_t *>(c->host_rb);
         cudaMemcpyAsync(h, off + nidx, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(h + 1, cmax, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
         st = wait_stream(c, "toeplitz table size");
         total = h[0];
+        c->toe_max_run = h[1];
     }
     if (st == SMART_OK && cudaMalloc(&c->toe_info, (size_t)nidx * sizeof(ToeInfo)) != cudaSuccess)
         st = fail(c, SMART_E_NOMEM, "cudaMalloc(toeplitz info) failed");
@@ -567,10 +572,19 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
     const bool averaged = c->norm == SMART_NORM_AVERAGED;
     if (averaged && (st = averaged_pixel_input(c, a.PX, &a.PX)) != SMART_OK) return st;
     if (a.n_gen < a.n) {
-        const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * TOE_CTAS_PER_SM);
+        // the smaller staging when every Toeplitz run of the tables fits it
+        const bool short_runs = c->toe_max_run <= NCAND_SHORT;
+        const int cps = short_runs ? toe_ctas_per_sm<NCAND_SHORT>() : toe_ctas_per_sm<NCAND>();
+        const unsigned grid = (unsigned)std::min<int64_t>(a.n_tiles, (int64_t)c->num_sms * cps);
         KernelTimer timer(c, SMART_KT_PIXEL_TOEPLITZ);
-        if (c->filter_kind == SMART_FILTER_POLY) k_pixel_toeplitz<SMART_FILTER_POLY><<<grid, NT, 0, c->stream>>>(a);
-        else k_pixel_toeplitz<SMART_FILTER_SCHIRMER><<<grid, NT, 0, c->stream>>>(a);
+        const bool poly = c->filter_kind == SMART_FILTER_POLY;
+        if (short_runs) {
+            if (poly) k_pixel_toeplitz<SMART_FILTER_POLY, NCAND_SHORT><<<grid, NT, 0, c->stream>>>(a);
+            else k_pixel_toeplitz<SMART_FILTER_SCHIRMER, NCAND_SHORT><<<grid, NT, 0, c->stream>>>(a);
+        } else {
+            if (poly) k_pixel_toeplitz<SMART_FILTER_POLY, NCAND><<<grid, NT, 0, c->stream>>>(a);
+            else k_pixel_toeplitz<SMART_FILTER_SCHIRMER, NCAND><<<grid, NT, 0, c->stream>>>(a);
+        }
         st = check_cuda(c, cudaGetLastError(), "k_pixel_toeplitz launch");
         if (st != SMART_OK) return st;
     }

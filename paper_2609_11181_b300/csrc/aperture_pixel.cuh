@@ -31,10 +31,17 @@ constexpr int TS_LOG2 = 8;
 constexpr int NT = 32;            // threads per CTA: one warp (its barriers are warp-wide)
 constexpr int RB = 8;             // consecutive slots per thread
 constexpr int NCAND = 120;        // longest Toeplitz candidate run kept in shared memory
-constexpr int SEGN = TS + NCAND + 8;
-static_assert(SEGN % 8 == 0, "staging layout works on rows of 8 pixels");
+constexpr int NCAND_SHORT = 64;   // contexts whose runs are all this short stage less
 static_assert(TS == NT * RB, "tile = threads x slots per thread");
-constexpr int TOE_CTAS_PER_SM = 11; // resident CTAs of the Toeplitz kernels (shared memory: 11 x 19 KB)
+static_assert(NCAND % 8 == 0 && NCAND_SHORT % 8 == 0, "staging layout works on rows of 8 pixels");
+// Shared-memory staging of a tile for runs of up to NC offsets: the bin-ring
+// segment (TS + NC + 8 pixels) and the geometry (NC entries), each double
+// buffered.  Resident CTAs per SM: the registers (168 a thread) allow 12;
+// the longer staging (19.2 KB a CTA) allows 11.
+template <int NC>
+constexpr int toe_segn() { return TS + NC + 8; }
+template <int NC>
+constexpr int toe_ctas_per_sm() { return NC <= NCAND_SHORT ? 12 : 11; }
 
 // shared-memory position of staged pixel m: rows of eight 16-byte pixels
 // (128 bytes, every bank once), the pixel's slot within its row XOR-ed with
@@ -361,11 +368,13 @@ __device__ __forceinline__ ToeStage tile_param(const MapArgs &a, const ToeStage 
 }
 
 // issue the copies of ring pair e of a tile into buffer b
+template <int NC>
 __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par, int64_t row0, int e, int jbase,
-                                          int nslots, float4 (*seg)[SEGN], float4 (*geo)[NCAND], int b, int tid) {
+                                          int nslots, float4 (*seg)[toe_segn<NC>()], float4 (*geo)[NC], int b,
+                                          int tid) {
     const ToeStage t = tile_param(a, par, row0, e, jbase);
     if (t.L > 0) {
-        const int nseg = min(SEGN, nslots + t.L + 7);
+        const int nseg = min(toe_segn<NC>(), nslots + t.L + 7);
         // -nr < k0 + m < 2 nr for every staged m (the window is shorter than the ring)
         for (int m = tid; m < nseg; m += NT) {
             int kk = t.k0 + m;
@@ -377,9 +386,10 @@ __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par,
     cp_async_commit();
 }
 
+template <int NC>
 struct ToeShared {
-    float4 seg[2][SEGN];
-    float4 geo[2][NCAND];
+    float4 seg[2][toe_segn<NC>()];
+    float4 geo[2][NC];
     int slot_t[TS];
     ToeStage par[TPN];
 };
@@ -414,8 +424,8 @@ struct ToeShared {
 // compensated (Kahan) total cost 13 % of the kernel's time (its registers
 // crowd the hot loop) for no accuracy the tests or the oracle comparison
 // can see.
-template <int KIND>
-__device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, ToeShared &S) {
+template <int KIND, int NC>
+__device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, ToeShared<NC> &S) {
     auto &seg = S.seg;
     auto &geo = S.geo;
     auto &slot_t = S.slot_t;
@@ -433,7 +443,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
     for (int64_t t = tb + tid; t < te; t += NT) slot_t[(int)(a.targets[t] - ring_start0) - jbase] = (int)(t - tb);
     __syncthreads();      // slot map and ring-pair parameters written
 
-    toe_stage(a, S.par, row0, 0, jbase, nslots, seg, geo, 0, tid);
+    toe_stage<NC>(a, S.par, row0, 0, jbase, nslots, seg, geo, 0, tid);
 
     const int s0 = RB * tid;
     bool any = false;
@@ -453,7 +463,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
         const int b = e & 1;
         cp_async_wait_all();
         __syncthreads();       // ring pair e staged; everyone is done with buffer b ^ 1
-        if (e + 1 < nent) toe_stage(a, S.par, row0, e + 1, jbase, nslots, seg, geo, b ^ 1, tid);
+        if (e + 1 < nent) toe_stage<NC>(a, S.par, row0, e + 1, jbase, nslots, seg, geo, b ^ 1, tid);
         const ToeStage cur = tile_param(a, S.par, row0, e, jbase);
         const int L = cur.L;
         if (L > 0 && any) {

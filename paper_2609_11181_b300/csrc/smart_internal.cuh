@@ -344,6 +344,7 @@ struct smart_ctx {
     int *d_work = nullptr;                           // tile counter of persistent launches
     smart::ToeInfo *toe_info = nullptr;              // Toeplitz tables of the pixel-mode ring pairs
     float4 *toe_geo = nullptr;
+    int toe_max_run = 0;                             // longest Toeplitz candidate run of the tables
     unsigned char *toe_ring = nullptr;               // per output ring: all ring pairs Toeplitz
     int32_t *gen_list = nullptr;                     // targets handled by the general kernel
     int64_t cap_gen_list = 0, n_gen = 0;

@@ -46,7 +46,7 @@ def test_batch_equals_single_maps(cuda_device):
     outs = batch.run()
     torch.cuda.synchronize()
     info = batch.info()
-    assert info["n_items"] > 0 and info["ctas_per_sm"] in (7, 9, 11)
+    assert info["n_items"] > 0 and info["ctas_per_sm"] in (7, 8, 9, 10, 11, 12)
     for s, o in zip(singles, outs):
         for k in ("map_e", "map_b", "var", "sum_w", "count", "members"):
             assert torch.equal(s[k], o[k]), k
