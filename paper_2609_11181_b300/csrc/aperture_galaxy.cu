@@ -187,8 +187,12 @@ __device__ __forceinline__ void gal_segment(const MapArgs &a, const BaryArgs &ba
                                             const float (&onf)[GT], int lo, int len,
                                             float (&pe)[GT], float (&pb)[GT], float (&pv)[GT], float (&pw)[GT],
                                             float (&nf)[GT], int (&nn)[GT], int (&nm)[GT]) {
-    // a generous pre-filter for the guard band; the exact test follows
-    const float Tmid = 0.5f * (a.Tlo + a.Thi), Thw = 0.5f * (a.Thi - a.Tlo) * 1.001f;
+    // a generous pre-filter for the guard band; the exact test follows.  The
+    // band (8e-6 T) is 67 to 134 float32 ulps of T wide; the pre-filter's
+    // half width is a quarter larger than the band's, far above the rounding
+    // of Tmid and of |s2 - Tmid| (half an ulp each), so that no pair at an
+    // edge of the band slips past both the member test and the band list
+    const float Tmid = 0.5f * (a.Tlo + a.Thi), Thw = 0.5f * (a.Thi - a.Tlo) * 1.25f;
     const float qn1 = a.f.qnorm * a.f.inv_ap2, qn2 = qn1 * a.f.inv_ap2;
     const int n1 = min(len, Rp.nr - lo);
 #pragma unroll 1

@@ -83,6 +83,64 @@ def test_maps_geometry_cases(cuda_device, ra0, dec0, rad, no, nb, th, filt):
     _check(px, rpx, "pixel")
 
 
+@pytest.mark.parametrize("th", [150.0, 300.0])
+def test_toeplitz_run_lengths(cuda_device, th):
+    """Equatorial rings at NSIDE 512 (6.9' pixels): a 150' aperture gives
+    Toeplitz runs of about 45 offsets (the 64-offset staging), a 300'
+    aperture runs of about 90 (the 120-offset staging)."""
+    ra0, dec0, rad = 10.0, 0.0, 2.0
+    cat = catalog(4242 + int(th), 120_000, ra0, dec0, rad + th / 60.0 + 0.5, nhalo=8, w_range=(0.5, 1.5))
+    tg = cap_targets(512, ra0, dec0, rad)
+    ctx, bf, px, _ = _gal_run(cuda_device, cat, tg, 512, 512, th, "schirmer")
+    assert ctx.general_targets().numel() < len(tg) // 4       # most targets on Toeplitz rings
+    rbf, rpx = _oracle_maps(cat, tg, 512, 512, th, 2)
+    _check(px, rpx, f"pixel {th}'")
+    _check(bf, rbf, f"brute {th}'")
+
+
+@pytest.mark.parametrize("th", [30.0, 300.0])
+def test_brute_force_members_at_the_band_edges(cuda_device, th):
+    """Galaxies placed at chord^2 = T (1 + r) from a target, with r stepping
+    by 2e-9 (a few hundredths of a float32 ulp) across both edges of the
+    float32 guard band (r = -+4e-6) and across T itself: every pair is
+    decided as the float64 definition decides it, so the member counts equal
+    the oracle's."""
+    nside = 256
+    T = api.chord2(th)
+    tg = cap_targets(nside, 30.0, 20.0, 1.5)[:40]
+    cv = oracle.pix2vec(nside, tg)
+    rng = np.random.default_rng(5)
+    rel = np.concatenate([c + 2e-9 * np.arange(-40, 41) for c in (-4e-6, 0.0, 4e-6)])
+    pts = []
+    for t in cv:
+        e = np.cross([0.0, 0.0, 1.0], t)
+        e /= np.linalg.norm(e)
+        n = np.cross(t, e)
+        d = 2.0 * np.arcsin(0.5 * np.sqrt(T * (1.0 + rel)))
+        b = rng.uniform(0.0, 2.0 * math.pi, rel.size)
+        v = (np.cos(d)[:, None] * t + np.sin(d)[:, None] * (np.cos(b)[:, None] * n + np.sin(b)[:, None] * e))
+        pts.append(v)
+    v = np.concatenate(pts)
+    ra = np.degrees(np.arctan2(v[:, 1], v[:, 0])) % 360.0
+    dec = np.degrees(np.arcsin(np.clip(v[:, 2], -1.0, 1.0)))
+    ng = ra.size
+    e1 = rng.normal(0.0, 0.2, ng)
+    e2 = rng.normal(0.0, 0.2, ng)
+    w = rng.uniform(0.5, 1.5, ng)
+    ref = oracle.map_galaxies(cv, ra, dec, e1, e2, w, 1, th * ARCMIN)
+    dev = cuda_device
+    ctx = api.Context(nside, th, "poly", nside_bin=1024)
+    ctx.set_targets(torch.from_numpy(tg).to(dev))
+    ctx.bin_galaxies(torch.from_numpy(ra).to(dev), torch.from_numpy(dec).to(dev),
+                     torch.from_numpy(e1).float().to(dev), torch.from_numpy(e2).float().to(dev),
+                     torch.from_numpy(w).float().to(dev))
+    got = ctx.map_bruteforce()
+    ctx.sync(60)
+    np.testing.assert_array_equal(got["count"].cpu().numpy(), ref["N"])
+    assert ctx.fp64_decisions() > 0
+    ctx.close()
+
+
 def test_pixel_mode_binned_field(cuda_device):
     """Pixel-based workload shape (Poisson counts, SIS field) at nside 512, Schirmer 10'."""
     nside = 512
