@@ -172,3 +172,19 @@ def test_query_disc_matches_all_pixels(nside):
         a = oracle.query_disc(nside, r0, th)
         b = oracle.query_disc(nside, r0, th, all_pixels=True)
         np.testing.assert_array_equal(np.sort(a), b)
+
+
+def test_pixel_sizes_printed_in_the_paper():
+    """The angular pixel sizes the paper prints for NSIDE 2048 to 16384
+    (tests/golden/pixel_sizes.json, with its citation) follow from the
+    oracle's ring structure: the pixel count (first pixel of the last ring
+    plus its length) divides the full sphere into equal areas."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pixel_sizes.json")))
+    for nside, printed in zip(g["nside"], g["pixel_size_arcmin"]):
+        first, count, _, _ = oracle.ring_info(nside, 4 * nside - 1)
+        npix = first + count
+        size = math.degrees(math.sqrt(4.0 * math.pi / npix)) * 60.0
+        assert round(size, 2) == printed, (nside, size, printed)
+
