@@ -256,4 +256,5 @@ def test_trained_network_improves_on_plain_pixel_map(cuda_device):
         corr_err.append(float(((corr.double() - b).pow(2).mean() / b.pow(2).mean()).sqrt()))
     p, q = float(np.mean(plain_err)), float(np.mean(corr_err))
     print(f"held-out rms(M - M_bf)/rms(M_bf): plain {p:.4f}, corrected {q:.4f} ({100 * (1 - q / p):.1f}% lower)")
-    assert q < p
+    # seeded data and bit-reproducible training: 0.3307 -> 0.3234 (2.2 %)
+    assert q <= 0.99 * p
