@@ -197,13 +197,13 @@ __device__ __forceinline__ void certain_run(const MapArgs &a, const RingPair &R,
 // pixel-mode general pair loop for one target and one ring pair; MODE picks
 // the sine series by the largest |u| of the ring pair (0: <= 0.05 rad,
 // 1: <= 0.45 rad, 2: |u| <= pi).  Offsets within hw_in are members for
-// certain: their loop has no test at all, and their galaxy count comes from
-// the count prefix.  The few offsets between hw_in and the window's edges
-// are tested; those inside the float32 guard band are only counted
-// (nband_out): they are decided in float64 once the target's other pairs
-// are summed.  A window that stays inside the bin ring's pixel range (all
-// but the targets next to the seam at azimuth 0) takes one run with no
-// wrapping arithmetic.
+// certain; the few offsets between hw_in and the window's edges are tested,
+// and the members among them join the run.  The run's pairs have no test at
+// all, and its galaxy count comes from the count prefix.  Offsets inside the
+// float32 guard band are only counted (nband_out): they are decided in
+// float64 once the target's other pairs are summed.  A window that stays
+// inside the bin ring's pixel range (all but the targets next to the seam
+// at azimuth 0) takes one run with no wrapping arithmetic.
 template <int KIND, int MODE>
 __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair &R, const TargetRing &tr,
                                                 const LatticeDiv &ld, const float4 *qtab, float &pe, float &pb,
@@ -216,13 +216,54 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
     int kl, kh;
     window(R, fr, kl, kh);
     int il = max(kl, (int)ceilf(-fr - R.hw_in)), ih = min(kh, (int)floorf(-fr + R.hw_in));
-    if (il > ih) {                        // no certain member: the whole window is tested
-        il = kh + 1;
-        ih = kh;
-    }
     const float u0 = fr * R.dphi;
-    const int len = ih - il + 1;
     const bool inside = Xi + kl >= 0 && Xi + kh < R.nr;
+    // The offsets outside the certain members are tested one by one, from the
+    // inside out (the same float32 chord^2 as the guard-band rescan): a member
+    // next to the run joins it (chord^2 grows with |u| on either side of the
+    // target, so the members form one interval), a member elsewhere is added
+    // alone, and the offsets inside the guard band are only counted (nband):
+    // they are decided in float64 once the target's other pairs are summed.
+    int nband = 0;
+    nband_out = 0;
+    if (kl > kh) return;      // no offset in the window
+    int ilc = il, ihc = ih;   // the tested sides start next to these
+    if (il > ih) {            // no certain member: the run grows from the offset nearest the target
+        const int ks = min(max(__float2int_rn(-fr), kl), kh);
+        const float u = fmaf((float)ks, R.dphi, u0);
+        float sinu, h;
+        sin_hav<MODE>(u, sinu, h);
+        const float s2 = fmaf(R.B, h, R.A);
+        ilc = ihc = ks;
+        if (s2 < a.Tlo) {
+            il = ih = ks;
+        } else {
+            nband += s2 <= a.Thi ? 1 : 0;
+            il = ks + 1;      // an empty run just above ks
+            ih = ks;
+        }
+    }
+    // below the run (kl <= k < ilc), then above it (ihc < k <= kh)
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int k0 = side == 0 ? kl : ihc + 1, k1 = side == 0 ? ilc - 1 : kh;
+        for (int i = 0; i <= k1 - k0; ++i) {
+            const int k = side == 0 ? k1 - i : k0 + i;      // from the run outward
+            const float u = fmaf((float)k, R.dphi, u0);
+            float sinu, h;
+            sin_hav<MODE>(u, sinu, h);
+            const float s2 = fmaf(R.B, h, R.A);
+            if (s2 < a.Tlo) {
+                if (side == 0 && k == il - 1) il = k;
+                else if (side == 1 && k == ih + 1) ih = k;
+                else pixel_pair<KIND, MODE>(a, R, qtab, u, R.start + (inside ? Xi + k : wrap_start(R, Xi, k)), pe, pb,
+                                            pv, pw, nn, nm);
+            } else {
+                nband += s2 <= a.Thi ? 1 : 0;
+            }
+        }
+    }
+    const int len = ih - il + 1;
     if (inside) {
         if (len > 0) {
             const int pbeg = R.start + Xi + il;
@@ -231,7 +272,7 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             nm += len;
         }
     } else if (len > 0) {
-        // certain members: bin pixels [kk0, nr) then [0, ...) when they wrap
+        // the run: bin pixels [kk0, nr) then [0, ...) when they wrap
         const int kk0 = wrap_start(R, Xi, il);
         const int n1 = min(len, R.nr - kk0);
 #pragma unroll 1
@@ -242,22 +283,6 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             certain_run<KIND, MODE>(a, R, qtab, u0, (float)(part == 0 ? il : il + n1), pbeg, cnt, pe, pb, pv, pw);
             nn += __ldg(a.NPRE + pbeg + cnt) - __ldg(a.NPRE + pbeg);
             nm += cnt;
-        }
-    }
-    // the offsets between the certain members and the window's edges
-    int nband = 0;
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {
-        const int ka = side == 0 ? kl : ih + 1, kb = side == 0 ? il - 1 : kh;
-        for (int k = ka; k <= kb; ++k) {
-            const float u = fmaf((float)k, R.dphi, u0);
-            float sinu, h;
-            sin_hav<MODE>(u, sinu, h);
-            const float s2 = fmaf(R.B, h, R.A);
-            if (s2 < a.Tlo)
-                pixel_pair<KIND, MODE>(a, R, qtab, u, R.start + (inside ? Xi + k : wrap_start(R, Xi, k)), pe, pb, pv,
-                                       pw, nn, nm);
-            else nband += s2 <= a.Thi ? 1 : 0;
         }
     }
     nband_out = nband;
