@@ -243,7 +243,10 @@ __device__ __forceinline__ void general_segment(const MapArgs &a, const RingPair
             ih = ks;
         }
     }
-    // below the run (kl <= k < ilc), then above it (ihc < k <= kh)
+    // below the run (kl <= k < ilc), then above it (ihc < k <= kh); most ring
+    // pairs have no such offset (the two half windows differ by a few
+    // hundredths of a pixel)
+    if (ilc > kl || ihc < kh)
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         const int k0 = side == 0 ? kl : ihc + 1, k1 = side == 0 ? ilc - 1 : kh;
