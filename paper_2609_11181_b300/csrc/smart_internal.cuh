@@ -115,9 +115,11 @@ __device__ __forceinline__ RingPix pix_to_ring(int64_t N, int64_t pix) {
         r.ring = (int)i;
         r.j = (int)(pix - 2 * i * (i - 1));
     } else if (pix < npix - ncap) {
+        // nside is a power of two: the division by the ring length 4N is a shift
         const int64_t ip = pix - ncap;
-        r.ring = (int)(ip / (4 * N) + N);
-        r.j = (int)(ip % (4 * N));
+        const int l = __ffsll((long long)N) + 1;      // log2(4N)
+        r.ring = (int)((ip >> l) + N);
+        r.j = (int)(ip & ((4 * N) - 1));
     } else {
         const int64_t ip = npix - pix;
         const int64_t is = (1 + isqrt64(2 * ip - 1)) >> 1;
