@@ -141,6 +141,23 @@ def test_brute_force_members_at_the_band_edges(cuda_device, th):
     ctx.close()
 
 
+@pytest.mark.parametrize("no,nb,th,filt,rad", [
+    (1024, 8192, 8.0, "poly", 1.0),      # fine bins: many short bin rings per output ring
+    (64, 256, 300.0, "poly", 3.0),       # a 5 degree aperture: the four-term series and the
+                                         # polynomial weight's d^2 / sin^2 d terms beyond the first
+])
+def test_maps_bin_and_aperture_extremes(cuda_device, no, nb, th, filt, rad):
+    ra0, dec0 = 140.0, -25.0
+    cat = catalog(int(th * 10) + nb, 150_000, ra0, dec0, rad + th / 60.0 + 0.5, nhalo=6, w_range=(0.5, 1.5),
+                  clumped=True)
+    tg = cap_targets(no, ra0, dec0, rad)
+    ctx, bf, px, _ = _gal_run(cuda_device, cat, tg, no, nb, th, filt)
+    rbf, rpx = _oracle_maps(cat, tg, no, nb, th, 1)
+    _check(bf, rbf, f"brute {no}/{nb}/{th}'")
+    _check(px, rpx, f"pixel {no}/{nb}/{th}'")
+    ctx.close()
+
+
 def test_pixel_mode_binned_field(cuda_device):
     """Pixel-based workload shape (Poisson counts, SIS field) at nside 512, Schirmer 10'."""
     nside = 512
