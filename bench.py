@@ -66,6 +66,14 @@ TOEPLITZ_EXEC_FLOPS_PER_PAIR = 11
 # weight sums 4, table 9, weight 5; the polynomial filter replaces table and
 # weight (14) by the chord-to-separation series, Q and Q / sin^2 d (18).
 GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 49, "jarvis": 49, "poly": 53}
+# The same for a general target that runs with its mirror image (one thread
+# for both; the image's pairs have the target's geometry with x -> -x): the
+# geometry, filter and weight of a pair (36 flop with a table, 40 with the
+# polynomial filter, as counted above) serve two pairs, each of which adds
+# its E / B, variance and weight sums (14) and shares Q^2: 31 measured with a
+# tabulated filter (ncu, as above, NSIDE 2048 case; 30.7), 33 polynomial
+# (the count's difference of 4 per two pairs added).
+GENERAL_PAIRED_EXEC_FLOPS_PER_PAIR = {"schirmer": 31, "jarvis": 31, "poly": 33}
 
 
 def _env_int(k, d):
@@ -265,8 +273,9 @@ def kernel_roofline(ctx, kernels: dict, workload: str, peak_tflops: float, peak_
     achieved = algorithmic flops per launch (the direct-form count per pair x
     member pairs) / its mean launch time, except for a kernel that shares work
     between pairs (the Toeplitz kernel: one geometry entry serves every target
-    at the same ring offset), which is held to the flops it executes.  Both
-    figures are reported per kernel."""
+    at the same ring offset; the general kernel with mirror pairs: one
+    geometry evaluation serves a target and its image), which is held to the
+    flops it executes.  Both figures are reported per kernel."""
     per = {}
     for name, (pairs, fpp, exec_fpp, sym, shares) in kernels.items():
         n, ms = ctx.timing_read(name)
@@ -415,6 +424,15 @@ def run_native_pixel(args, world, rank):
     pairs_step = int(members.sum().item())
     gen_idx = ctx.general_targets()
     pairs_gen = int(members[gen_idx].sum().item()) if gen_idx.numel() else 0
+    gen_pairs, gen_single = ctx.general_pairs()
+    pairs_mirror = int(members[gen_pairs.reshape(-1)].sum().item()) if gen_pairs.numel() else 0
+    # launches per map: the mirror pairs (with up to a sixteenth as many
+    # unpaired targets run ahead of them), else the unpaired targets alone
+    npg = int(gen_pairs.shape[0])
+    gen_launches = int(npg > 0) + int(gen_single > 0 and not (npg > 0 and 16 * gen_single <= npg))
+    gen_exec = ((pairs_mirror * GENERAL_PAIRED_EXEC_FLOPS_PER_PAIR[wl.filter]
+                 + (pairs_gen - pairs_mirror) * GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter]) / pairs_gen
+                if pairs_gen else GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(torch.cuda.current_device())
     barrier(world)
@@ -440,12 +458,14 @@ def run_native_pixel(args, world, rank):
     peak, peak_src = fp32_peak(peaks_live)
     roof, per_kernel = kernel_roofline(
         ctx, {"pixel_toeplitz": (pairs_step - pairs_gen, algo, TOEPLITZ_EXEC_FLOPS_PER_PAIR, "k_pixel_toeplitz", True),
-              "pixel_general": (pairs_gen, algo, GENERAL_EXEC_FLOPS_PER_PAIR[wl.filter], "k_pixel_general", False),
+              "pixel_general": (pairs_gen, algo, round(gen_exec, 1), "k_pixel_general", pairs_mirror > 0),
               "pixel_band": (0, None, None, "k_pixel_band", False)},
         args.workload, peak, peak_src)
     ctx.timing(False)
     npix_bin = 12 * wl.nside ** 2
-    launches_step = sum(v["launches"] for v in per_kernel.values()) / args.steps + scan_launches(npix_bin + 1)
+    # the general timer spans the mirror-pair and the unpaired launch of a map
+    launches_step = (sum(v["launches"] for v in per_kernel.values()) / args.steps + scan_launches(npix_bin + 1)
+                     + (gen_launches - 1 if "pixel_general" in per_kernel else 0))
     map_roof = {"achieved": round(pairs_step * algo / (ms_step * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
                 "peak": peak, "frac": round(pairs_step * algo / (ms_step * 1e-3) / 1e12 / peak, 4),
                 "basis": f"whole step: member pairs x {algo} algorithmic flop per pair / ms_per_step"}
@@ -543,6 +563,9 @@ def run_native_pixel(args, world, rank):
         "roofline": roof,
         "map_roofline": map_roof,
         "kernels": per_kernel,
+        "general_mirror_pairs": {"pairs": int(gen_pairs.shape[0]), "unpaired_targets": gen_single,
+                                 "member_pairs_of_paired_targets": pairs_mirror,
+                                 "member_pairs_general": pairs_gen, "launches_per_map": gen_launches},
         "fma_peaks_measured": peaks_live,
         "e2e": {"value": round(pairs_all / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gpair/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 3),

@@ -397,6 +397,22 @@ smart_status smart_timing_read(smart_ctx *ctx, int kernel, int64_t *launches, do
 smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_gen);
 
 /*
+ * The general kernel's mirror pairs (a design of this library; the paper has
+ * no counterpart).  Every HEALPix ring is symmetric about the meridians
+ * phi = m pi/4, so a general target whose mirror image about one of them is
+ * a target as well shares each pair's geometry with it: such pairs are
+ * found once per target set (meridians 0, pi/2, pi/4, 3 pi/4 in that order,
+ * each target in at most one pair) and run in one thread each.  *n_pairs and
+ * *n_single (host) receive the number of pairs and of general targets left
+ * unpaired (n_gen = 2 n_pairs + n_single); pairs (device, int32, capacity
+ * cap pairs) receives the pairs' target positions as (lower, image) unless
+ * NULL.  SMART_E_STATE before the first pixel map after smart_set_targets.
+ * Asynchronous on the context stream.
+ */
+smart_status smart_get_general_pairs(smart_ctx *ctx, int32_t *pairs, int64_t cap, int64_t *n_pairs,
+                                     int64_t *n_single);
+
+/*
  * FMA throughput probe (diagnostics; the paper has no counterpart).  Enqueues
  * one kernel of ctas_per_sm (1..8) CTAs of 256 threads per SM on the stream;
  * every thread runs iters x 128 fused multiply-add instructions in eight

@@ -69,6 +69,7 @@ SIGNATURES = {
     "smart_timing_enable": (_I32, [_VP, _I32]),
     "smart_timing_read": (_I32, [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_D), _D]),
     "smart_get_general_targets": (_I32, [_VP, _VP, _I64, ctypes.POINTER(_I64)]),
+    "smart_get_general_pairs": (_I32, [_VP, _VP, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "smart_set_band_slot_limit": (_I32, [_VP, _I64]),
     "smart_mlp_features": (_I32, [_VP, ctypes.POINTER(SmartMaps), ctypes.POINTER(SmartMaps), _VP, _VP, _VP, _VP]),
     "smart_mlp_create": (_I32, [_I32, _VP, ctypes.POINTER(_VP)]),

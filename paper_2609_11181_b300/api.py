@@ -269,6 +269,22 @@ class Context:
         self.sync(60)
         return idx.long()
 
+    def general_pairs(self):
+        """The general kernel's mirror pairs: (pairs [n_pairs, 2] int64 on the
+        device, target positions (lower, image)), and the number of general
+        targets left unpaired."""
+        npairs, nsingle = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.smart_get_general_pairs(self._h, None, 0, ctypes.byref(npairs), ctypes.byref(nsingle)),
+                    "smart_get_general_pairs")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        pairs = torch.empty((int(npairs.value), 2), dtype=torch.int32, device=dev)
+        if pairs.numel():
+            self._check(self._lib.smart_get_general_pairs(self._h, _ptr(pairs, torch.int32, "pairs"), pairs.shape[0],
+                                                          ctypes.byref(npairs), ctypes.byref(nsingle)),
+                        "smart_get_general_pairs")
+        self.sync(60)
+        return pairs.long(), int(nsingle.value)
+
     def set_band_slot_limit(self, n_slots: int):
         """Testing aid: cap the general kernel's guard-band slots (0: default)."""
         self._check(self._lib.smart_set_band_slot_limit(self._h, int(n_slots)), "smart_set_band_slot_limit")

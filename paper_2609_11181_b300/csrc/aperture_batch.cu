@@ -47,40 +47,63 @@ __global__ void __launch_bounds__(NT, toe_ctas_per_sm<NC>()) k_pixel_batched(con
     }
 }
 
-// the general targets of every map: one thread per (map, target) entry.
-// The list runs map by map, so the filter table of the block's first map is
-// staged in shared memory; entries of another map read theirs from global.
+// the general targets of every map: one thread per entry (map, target, its
+// mirror image or -1, 0) of the list, whose first np entries are the mirror
+// pairs of every map and the rest the unpaired targets.  Thread i of the
+// pair launch takes entry np + i for i < n_lead (unpaired targets run ahead
+// of the pairs, see gen_lead) and entry i - n_lead after that; the unpaired
+// launch takes entries lo + i.  The list runs map by map within each part,
+// so the filter table of the block's first map is staged in shared memory;
+// entries of another map read theirs from global memory.
 template <int KIND>
-__global__ void __launch_bounds__(128, 7) k_pixel_batched_general(const MapArgs *__restrict__ maps,
-                                                                   const int2 *__restrict__ list, int64_t n,
-                                                                   const GenBand gb) {
-    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
-    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x;
-    const int m0 = list[i0].x;
+__device__ __forceinline__ void batched_general(const MapArgs *__restrict__ maps, const int4 *__restrict__ list,
+                                                int64_t i, bool pair, int64_t first, const GenBand &gb,
+                                                float4 *qtab) {
+    const int m0 = list[first].x;
     if (KIND != SMART_FILTER_POLY) {
         const float4 *src = maps[m0].f.qtab;
         for (int k = threadIdx.x; k < QTAB_BINS; k += blockDim.x) qtab[k] = src[k];
         __syncthreads();
     }
-    const int64_t i = i0 + threadIdx.x;
-    if (i >= n) return;
-    const int2 e = list[i];
+    if (i < 0) return;
+    const int4 e = list[i];
     const MapArgs &a = maps[e.x];
-    general_target<KIND>(a, e.y, i, e.x == m0 ? qtab : a.f.qtab, gb);
+    if (pair) general_target2<KIND>(a, e.y, e.z, i, e.x == m0 ? qtab : a.f.qtab, gb);
+    else general_target<KIND>(a, e.y, i, e.x == m0 ? qtab : a.f.qtab, gb);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 7) k_pixel_batched_general(const MapArgs *__restrict__ maps,
+                                                                  const int4 *__restrict__ list, int64_t lo,
+                                                                  int64_t hi, const GenBand gb) {
+    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
+    const int64_t first = lo + blockIdx.x * (int64_t)blockDim.x, i = first + threadIdx.x;
+    batched_general<KIND>(maps, list, i < hi ? i : -1, false, first, gb, qtab);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128, GEN_PAIR_CTAS_PER_SM) k_pixel_batched_general_pairs(
+    const MapArgs *__restrict__ maps, const int4 *__restrict__ list, int64_t np, int64_t n_lead, const GenBand gb) {
+    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x, i = i0 + threadIdx.x;
+    const int64_t first = i0 < n_lead ? np + i0 : i0 - n_lead;
+    const int64_t e = i < n_lead ? np + i : (i - n_lead < np ? i - n_lead : -1);
+    batched_general<KIND>(maps, list, e, i >= n_lead, first, gb, qtab);
 }
 
 // the general targets with guard-band pairs, one thread per slot
 template <int KIND>
-__global__ void k_pixel_batched_band(const MapArgs *__restrict__ maps, const int2 *__restrict__ list,
+__global__ void k_pixel_batched_band(const MapArgs *__restrict__ maps, const int4 *__restrict__ list,
                                      const GenBand gb) {
     const unsigned long long n = min(*gb.counts, (unsigned long long)gb.cap_slots);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        const int2 e = list[gb.idx[i]];
+        const int64_t tag = gb.idx[i];
+        const int4 e = list[tag >> 1];
         const MapArgs &a = maps[e.x];
         const double *raw = gb.raw + 4 * i;
-        band_finish<KIND>(a, e.y, a.f.qtab, gb.mask[i], raw[0], raw[1], raw[2], raw[3], gb.cnt[2 * i],
-                          gb.cnt[2 * i + 1]);
+        band_finish<KIND>(a, (tag & 1) ? e.z : e.y, e.y, a.f.qtab, gb.mask[i], raw[0], raw[1], raw[2], raw[3],
+                          gb.cnt[2 * i], gb.cnt[2 * i + 1]);
     }
 }
 
@@ -100,8 +123,10 @@ struct smart_batch {
     MapArgs *d_maps = nullptr;
     BatchItem *d_items = nullptr;
     int64_t n_items = 0;
-    int2 *d_gen = nullptr;           // (map, target) of every general target
-    int64_t n_gen = 0;
+    int4 *d_gen = nullptr;           // general work: (map, target, its mirror image or -1, 0)
+    int64_t n_gen = 0;               // entries of d_gen
+    int64_t n_gen_pairs = 0;         // the first n_gen_pairs of them are mirror pairs
+    int64_t n_gen_targets = 0;       // targets they cover
     void *d_band = nullptr;          // slots of general targets with guard-band pairs
     unsigned long long *d_band_count = nullptr;
     GenBand gb{};
@@ -153,14 +178,23 @@ static smart_status batch_launch(smart_batch *b, int ctas_per_sm, int order) {
     }
     if (b->n_gen > 0) {
         cudaStream_t gs = fork ? b->side : b->stream;
-        const unsigned grid = (unsigned)((b->n_gen + 127) / 128);
         if (cudaMemsetAsync(b->d_band_count, 0, sizeof(unsigned long long), gs) != cudaSuccess)
             return bfail(b, SMART_E_CUDA, "slot counter reset failed");
+        const int64_t np = b->n_gen_pairs, ng = b->n_gen, n_lead = gen_lead(np, ng - np);
+        const unsigned gp = (unsigned)((np + n_lead + 127) / 128), g1 = (unsigned)((ng - np - n_lead + 127) / 128);
         if (b->kind == SMART_FILTER_POLY) {
-            k_pixel_batched_general<SMART_FILTER_POLY><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen, b->gb);
+            if (np > 0)
+                k_pixel_batched_general_pairs<SMART_FILTER_POLY><<<gp, 128, 0, gs>>>(b->d_maps, b->d_gen, np, n_lead, b->gb);
+            if (ng > np + n_lead)
+                k_pixel_batched_general<SMART_FILTER_POLY><<<g1, 128, 0, gs>>>(b->d_maps, b->d_gen, np + n_lead, ng, b->gb);
             k_pixel_batched_band<SMART_FILTER_POLY><<<4 * sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
         } else {
-            k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, gs>>>(b->d_maps, b->d_gen, b->n_gen, b->gb);
+            if (np > 0)
+                k_pixel_batched_general_pairs<SMART_FILTER_SCHIRMER><<<gp, 128, 0, gs>>>(b->d_maps, b->d_gen, np, n_lead,
+                                                                                        b->gb);
+            if (ng > np + n_lead)
+                k_pixel_batched_general<SMART_FILTER_SCHIRMER><<<g1, 128, 0, gs>>>(b->d_maps, b->d_gen, np + n_lead, ng,
+                                                                                  b->gb);
             k_pixel_batched_band<SMART_FILTER_SCHIRMER><<<4 * sms, 128, 0, gs>>>(b->d_maps, b->d_gen, b->gb);
         }
     }
@@ -264,7 +298,7 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     smart_status st = SMART_OK;
     std::vector<BatchItem> items;
     std::vector<double> cost;
-    std::vector<int2> gen;
+    std::vector<int4> gen, gen_single;
     for (int m = 0; m < n_maps && st == SMART_OK; ++m) {
         smart_ctx *c = ctxs[m];
         cudaStream_t keep = c->stream;
@@ -305,11 +339,13 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
                 cost.push_back((double)(tiles[t + 1] - tiles[t]) * pix_per_ap);
             }
         }
-        if (a.n_gen > 0 && st == SMART_OK) {
-            std::vector<int32_t> gl(a.n_gen);
-            cudaMemcpyAsync(gl.data(), a.gen_list, (size_t)a.n_gen * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream);
+        if (a.n_work > 0 && st == SMART_OK) {
+            std::vector<int2> gw(a.n_work);
+            cudaMemcpyAsync(gw.data(), a.gen_work, (size_t)a.n_work * sizeof(int2), cudaMemcpyDeviceToHost, b->stream);
             if (cudaStreamSynchronize(b->stream) != cudaSuccess) st = bfail(b, SMART_E_CUDA, "general list download failed");
-            for (int64_t g = 0; g < a.n_gen && st == SMART_OK; ++g) gen.push_back(make_int2(m, gl[g]));
+            for (int64_t g = 0; g < a.n_work && st == SMART_OK; ++g)
+                (g < a.n_pairs ? gen : gen_single).push_back(make_int4(m, gw[g].x, gw[g].y, 0));
+            b->n_gen_targets += a.n_gen;
         }
         c->stream = keep;
     }
@@ -325,21 +361,23 @@ extern "C" smart_status smart_batch_create(smart_ctx *const *ctxs, const smart_m
     b->by_cost.resize(items.size());
     for (size_t i = 0; i < idx.size(); ++i) b->by_cost[i] = items[idx[i]];
     const size_t nb = std::max<size_t>(1, items.size());
+    b->n_gen_pairs = (int64_t)gen.size();
+    gen.insert(gen.end(), gen_single.begin(), gen_single.end());
     b->n_gen = (int64_t)gen.size();
     if (cudaMalloc(&b->d_maps, sizeof(MapArgs) * n_maps) != cudaSuccess ||
         cudaMalloc(&b->d_items, sizeof(BatchItem) * 2 * nb) != cudaSuccess ||
-        cudaMalloc(&b->d_gen, sizeof(int2) * std::max<size_t>(1, gen.size())) != cudaSuccess ||
+        cudaMalloc(&b->d_gen, sizeof(int4) * std::max<size_t>(1, gen.size())) != cudaSuccess ||
         cudaMalloc(&b->d_work, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->d_band, (size_t)(GEN_BAND_SLOT_BYTES * gen_band_slots(b->n_gen))) != cudaSuccess ||
+        cudaMalloc(&b->d_band, (size_t)(GEN_BAND_SLOT_BYTES * gen_band_slots(b->n_gen_targets))) != cudaSuccess ||
         cudaMalloc(&b->d_band_count, sizeof(unsigned long long)) != cudaSuccess) {
         bfail(b, SMART_E_NOMEM, "cudaMalloc(batch tables) failed");
         smart_batch_destroy(b);
         return SMART_E_NOMEM;
     }
-    b->gb = gen_band_layout(b->d_band, gen_band_slots(b->n_gen), b->d_band_count);
+    b->gb = gen_band_layout(b->d_band, gen_band_slots(b->n_gen_targets), b->d_band_count);
     cudaMemcpyAsync(b->d_maps, b->args.data(), sizeof(MapArgs) * n_maps, cudaMemcpyHostToDevice, b->stream);
     if (!gen.empty())
-        cudaMemcpyAsync(b->d_gen, gen.data(), sizeof(int2) * gen.size(), cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(b->d_gen, gen.data(), sizeof(int4) * gen.size(), cudaMemcpyHostToDevice, b->stream);
     if (!items.empty()) {
         cudaMemcpyAsync(b->d_items, b->by_cost.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_items + items.size(), b->natural.data(), sizeof(BatchItem) * items.size(),

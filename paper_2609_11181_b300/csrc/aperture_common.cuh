@@ -51,6 +51,8 @@ struct MapArgs {
     const unsigned char *toe_ring;  // 1: every ring pair of this output ring is Toeplitz
     const int32_t *gen_list;        // targets of the other rings (general kernel)
     int64_t n_gen;
+    const int2 *gen_work;           // general kernel's work: n_pairs (target, mirror image), then (target, -1)
+    int64_t n_work, n_pairs;
     int *work;               // tile counter of the persistent launch
     // brute-force inputs
     const int32_t *offsets;

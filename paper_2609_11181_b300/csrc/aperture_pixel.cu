@@ -163,8 +163,9 @@ __global__ void __launch_bounds__(NT, toe_ctas_per_sm<NC>()) k_pixel_toeplitz(co
 }
 
 // ------------------------------------------------------------------------
-// General kernel: one thread per target of the other rings; consecutive
-// threads hold consecutive targets, so bin pixels are read coalesced.
+// General kernel: one thread per target of the other rings, or per mirror
+// pair of them (k_pixel_general_pairs); consecutive threads hold consecutive
+// targets, so bin pixels are read coalesced.
 // ------------------------------------------------------------------------
 template <int KIND>
 __global__ void __launch_bounds__(128, 7) k_pixel_general(const __grid_constant__ MapArgs a, const GenBand gb) {
@@ -173,9 +174,32 @@ __global__ void __launch_bounds__(128, 7) k_pixel_general(const __grid_constant_
         for (int i = threadIdx.x; i < QTAB_BINS; i += blockDim.x) qtab[i] = a.f.qtab[i];
         __syncthreads();
     }
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= a.n_gen) return;
-    general_target<KIND>(a, a.gen_list[idx], idx, qtab, gb);
+    const int64_t idx = a.n_pairs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= a.n_work) return;
+    general_target<KIND>(a, a.gen_work[idx].x, idx, qtab, gb);
+}
+
+// the mirror pairs; n_lead unpaired targets (all of them when they are few)
+// run first, in the leading threads, so that they finish alongside the pairs
+// rather than as a launch of their own after them
+template <int KIND>
+__global__ void __launch_bounds__(128, GEN_PAIR_CTAS_PER_SM) k_pixel_general_pairs(const __grid_constant__ MapArgs a,
+                                                                                  const GenBand gb, int64_t n_lead) {
+    __shared__ float4 qtab[KIND == SMART_FILTER_POLY ? 1 : QTAB_BINS];
+    if (KIND != SMART_FILTER_POLY) {
+        for (int i = threadIdx.x; i < QTAB_BINS; i += blockDim.x) qtab[i] = a.f.qtab[i];
+        __syncthreads();
+    }
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_lead) {
+        const int64_t idx = a.n_pairs + i;
+        general_target<KIND>(a, a.gen_work[idx].x, idx, qtab, gb);
+        return;
+    }
+    const int64_t idx = i - n_lead;
+    if (idx >= a.n_pairs) return;
+    const int2 w = a.gen_work[idx];
+    general_target2<KIND>(a, w.x, w.y, idx, qtab, gb);
 }
 
 // the general kernel's targets with guard-band pairs, one thread per slot:
@@ -191,8 +215,10 @@ __global__ void k_pixel_band(const MapArgs a, const GenBand gb) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const double *raw = gb.raw + 4 * i;
-        band_finish<KIND>(a, a.gen_list[gb.idx[i]], qtab, gb.mask[i], raw[0], raw[1], raw[2], raw[3], gb.cnt[2 * i],
-                          gb.cnt[2 * i + 1]);
+        const int64_t tag = gb.idx[i];
+        const int2 w = a.gen_work[tag >> 1];
+        band_finish<KIND>(a, (tag & 1) ? w.y : w.x, w.x, qtab, gb.mask[i], raw[0], raw[1], raw[2], raw[3],
+                          gb.cnt[2 * i], gb.cnt[2 * i + 1]);
     }
 }
 
@@ -219,6 +245,66 @@ __global__ void k_gen_scatter(const int32_t *__restrict__ flag, const int32_t *_
                               int32_t *__restrict__ list) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         if (flag[k]) list[idx[k]] = (int32_t)k;
+}
+
+// position of p in the ascending list t[0 .. n), or -1
+template <typename T>
+__device__ __forceinline__ int64_t find_sorted(const T *__restrict__ t, int64_t n, T p) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(t + mid) < p) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n && __ldg(t + lo) == p ? lo : -1;
+}
+
+// One round of mirror pairing of the general targets about the meridian
+// m pi/4: a target not paired in an earlier round is paired with its image
+// on the same ring (general as well: same ring) when the image is a target
+// not paired in an earlier round.  pair[g] = (general-list position of the
+// partner, round), or (-1, -1).  The image map is an involution, so within a
+// round g and its image decide alike and no third target is involved; a
+// partner's entry read during the round is either unset or already (g, round).
+__global__ void k_gen_pair_round(const int64_t *__restrict__ targets, int64_t n, int64_t N0,
+                                 const int32_t *__restrict__ gen_list, int64_t ng, int m, int round,
+                                 int2 *__restrict__ pair) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        if (pair[g].x >= 0) continue;
+        const int64_t pix = __ldg(targets + __ldg(gen_list + g));
+        const TargetRing tr = target_ring(N0, pix);
+        int j2 = (m * tr.q0 - tr.s0 - tr.j0) % tr.nr0;
+        j2 += j2 < 0 ? tr.nr0 : 0;
+        if (j2 == tr.j0) continue;                   // on the mirror line itself
+        const int64_t t2 = find_sorted<int64_t>(targets, n, pix - tr.j0 + j2);
+        if (t2 < 0) continue;
+        const int64_t g2 = find_sorted<int32_t>(gen_list, ng, (int32_t)t2);
+        if (g2 < 0) continue;
+        const int2 q = __ldcg(pair + g2);
+        if (q.x >= 0 && q.y != round) continue;
+        pair[g] = make_int2((int)g2, round);
+    }
+}
+
+__global__ void k_gen_work_flags(const int2 *__restrict__ pair, int64_t ng, int32_t *__restrict__ f_pair,
+                                 int32_t *__restrict__ f_single) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int p = pair[g].x;
+        f_pair[g] = p > g ? 1 : 0;
+        f_single[g] = p < 0 ? 1 : 0;
+    }
+}
+
+// the work list: the pairs (lower position first) in list order, then the
+// unpaired targets in list order
+__global__ void k_gen_work_scatter(const int2 *__restrict__ pair, const int32_t *__restrict__ gen_list, int64_t ng,
+                                   const int32_t *__restrict__ i_pair, const int32_t *__restrict__ i_single,
+                                   int64_t n_pairs, int2 *__restrict__ work) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int p = pair[g].x;
+        if (p > g) work[i_pair[g]] = make_int2(gen_list[g], gen_list[p]);
+        else if (p < 0) work[n_pairs + i_single[g]] = make_int2(gen_list[g], -1);
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -392,6 +478,49 @@ static smart_status build_toeplitz(smart_ctx *c, const MapArgs &a) {
     return st;
 }
 
+// the general kernel's work list: mirror pairs found in four rounds (the
+// meridians 0, pi/2, pi/4, 3 pi/4), then the targets left unpaired
+static smart_status build_gen_work(smart_ctx *c, int64_t ng) {
+    smart_status st = ensure_alloc(c, (void **)&c->gen_work, c->cap_gen_work, ng, sizeof(int2), "general work list");
+    if (st != SMART_OK) return st;
+    c->n_work = c->n_work_pairs = 0;
+    if (ng == 0) return SMART_OK;
+    const size_t words = (size_t)(ng + 1);
+    char *scratch = nullptr;
+    if (cudaMallocAsync((void **)&scratch, words * (sizeof(int2) + 4 * sizeof(int32_t)), c->stream) != cudaSuccess)
+        return fail(c, SMART_E_NOMEM, "cudaMallocAsync(mirror pairs) failed");
+    int2 *pair = (int2 *)scratch;
+    int32_t *f_pair = (int32_t *)(pair + words), *f_single = f_pair + words, *i_pair = f_single + words,
+            *i_single = i_pair + words;
+    const unsigned blocks = (unsigned)std::min<int64_t>((ng + 255) / 256, 148 * 32);
+    st = check_cuda(c, cudaMemsetAsync(pair, 0xFF, (size_t)ng * sizeof(int2), c->stream), "mirror pairs");
+    const int lines[4] = {0, 2, 1, 3};
+    for (int r = 0; r < 4 && st == SMART_OK; ++r) {
+        k_gen_pair_round<<<blocks, 256, 0, c->stream>>>(c->targets, c->n_targets, c->nside_out, c->gen_list, ng,
+                                                         lines[r], r, pair);
+        st = check_cuda(c, cudaGetLastError(), "k_gen_pair_round");
+    }
+    if (st == SMART_OK) {
+        k_gen_work_flags<<<blocks, 256, 0, c->stream>>>(pair, ng, f_pair, f_single);
+        st = exclusive_scan_i32(c, f_pair, i_pair, ng, ng + 1);
+    }
+    if (st == SMART_OK) st = exclusive_scan_i32(c, f_single, i_single, ng, ng + 1);
+    int32_t *tot = reinterpret_cast<int32_t *>(c->host_rb);
+    if (st == SMART_OK) {
+        cudaMemcpyAsync(&tot[0], i_pair + ng, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(&tot[1], i_single + ng, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+        st = wait_stream(c, "general work count");
+    }
+    if (st == SMART_OK) {
+        k_gen_work_scatter<<<blocks, 256, 0, c->stream>>>(pair, c->gen_list, ng, i_pair, i_single, tot[0], c->gen_work);
+        st = check_cuda(c, cudaGetLastError(), "general work list");
+        c->n_work = (int64_t)tot[0] + tot[1];
+        c->n_work_pairs = tot[0];
+    }
+    cudaFreeAsync(scratch, c->stream);
+    return st;
+}
+
 // which output rings go to the Toeplitz kernel, and the list of targets for
 // the general kernel (once per target set)
 static smart_status build_ring_classes(smart_ctx *c, const MapArgs &a) {
@@ -420,6 +549,8 @@ static smart_status build_ring_classes(smart_ctx *c, const MapArgs &a) {
     st = check_cuda(c, cudaGetLastError(), "general target list");
     if (st != SMART_OK) return st;
     c->n_gen = ng;
+    st = build_gen_work(c, ng);
+    if (st != SMART_OK) return st;
     c->gen_version = c->targets_version;
     return SMART_OK;
 }
@@ -506,6 +637,9 @@ smart_status prepare_pixel(smart_ctx *c, const smart_maps *out, MapArgs &a) {
     a.toe_ring = c->toe_ring;
     a.gen_list = c->gen_list;
     a.n_gen = a.n > 0 ? c->n_gen : 0;
+    a.gen_work = c->gen_work;
+    a.n_work = a.n > 0 ? c->n_work : 0;
+    a.n_pairs = a.n > 0 ? c->n_work_pairs : 0;
     return SMART_OK;
 }
 
@@ -593,10 +727,18 @@ extern "C" smart_status smart_map_pixel(smart_ctx *c, const smart_maps *out) {
         if ((st = general_band_buffers(c, a.n_gen, gb)) != SMART_OK) return st;
         const bool poly = c->filter_kind == SMART_FILTER_POLY;
         {
-            const unsigned grid = (unsigned)((a.n_gen + 127) / 128);
             KernelTimer timer(c, SMART_KT_PIXEL_GENERAL);
-            if (poly) k_pixel_general<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a, gb);
-            else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a, gb);
+            const int64_t n_single = a.n_work - a.n_pairs, n_lead = gen_lead(a.n_pairs, n_single);
+            if (a.n_pairs > 0) {
+                const unsigned grid = (unsigned)((a.n_pairs + n_lead + 127) / 128);
+                if (poly) k_pixel_general_pairs<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a, gb, n_lead);
+                else k_pixel_general_pairs<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a, gb, n_lead);
+            }
+            if (n_single > n_lead) {
+                const unsigned grid = (unsigned)((n_single + 127) / 128);
+                if (poly) k_pixel_general<SMART_FILTER_POLY><<<grid, 128, 0, c->stream>>>(a, gb);
+                else k_pixel_general<SMART_FILTER_SCHIRMER><<<grid, 128, 0, c->stream>>>(a, gb);
+            }
         }
         {
             KernelTimer timer(c, SMART_KT_PIXEL_BAND);

@@ -14,11 +14,13 @@
 //    targets: 4 FMAs + 1 FMA (noise) + 1 add (weight) per pair.
 //  * general path (polar rings, unequal rings, unequal nside): per pair
 //    geometry from the ring-pair constants, the filter from a cubic table
-//    (Schirmer) or in closed form (polynomial).
+//    (Schirmer) or in closed form (polynomial).  A target and its mirror
+//    image about a meridian m pi/4 share that geometry (general_target2).
 //
 // Sums: float32 within one ring pair (Toeplitz: two ring pairs); across ring
-// pairs float32 totals (Toeplitz) or compensated (Kahan) totals (general
-// path); the weight sum goes to float64 for the final normalisation.
+// pairs float32 totals (Toeplitz, mirror pairs) or compensated (Kahan)
+// totals (other general targets); the weight sum goes to float64 for the
+// final normalisation.
 #pragma once
 
 #include "aperture_common.cuh"
@@ -32,6 +34,15 @@ constexpr int NT = 32;            // threads per CTA: one warp (its barriers are
 constexpr int RB = 8;             // consecutive slots per thread
 constexpr int NCAND = 120;        // longest Toeplitz candidate run kept in shared memory
 constexpr int NCAND_SHORT = 64;   // contexts whose runs are all this short stage less
+constexpr int GEN_PAIR_CTAS_PER_SM = 4;  // general kernel, mirror pairs: resident 128-thread CTAs per SM
+// unpaired general targets that run in the mirror-pair launch (ahead of the
+// pairs) instead of a launch of their own: all of them when they are at most
+// a sixteenth of the pairs (a launch of their own would run after the pairs,
+// a short tail with the GPU nearly idle), else none (their own launch keeps
+// seven CTAs per SM)
+inline int64_t gen_lead(int64_t n_pairs, int64_t n_single) {
+    return n_pairs > 0 && 16 * n_single <= n_pairs ? n_single : 0;
+}
 static_assert(TS == NT * RB, "tile = threads x slots per thread");
 static_assert(NCAND % 8 == 0 && NCAND_SHORT % 8 == 0, "staging layout works on rows of 8 pixels");
 // Shared-memory staging of a tile for runs of up to NC offsets: the bin-ring
@@ -95,17 +106,31 @@ __device__ __forceinline__ void pixel_pair(const MapArgs &a, const RingPair &R, 
     nm += 1;
 }
 
+// bin-ring index of the mirror image of bin pixel kk (0 <= kk < nr) about
+// the meridian m pi/4: (m q - s - kk) mod nr for a ring of nr = 4 q pixels
+// centred at azimuths (k + s/2) 2 pi / nr; cm = m q - s lies in [-1, 3 q]
+__device__ __forceinline__ int mirror_index(const RingPair &R, int cm, int kk) {
+    const int v = cm - kk;
+    return v < 0 ? v + R.nr : v;
+}
+
 // the guard-band pairs of one target and one ring pair, decided in float64
-// (window, u and s^2 exactly as in general_segment)
+// (window, u and s^2 exactly as in general_segment).  mline < 0: the pairs
+// of target pix itself (tr is its ring).  mline = m >= 0: pix is the mirror
+// image about the meridian m pi/4 of the target whose ring position tr
+// holds; the window, u and s^2 are that target's, the bin pixels their
+// mirror images and the azimuth offsets -u (as in general_segment2).
 template <int KIND, int MODE>
 __device__ __forceinline__ void band_pairs(const MapArgs &a, const RingPair &R, const TargetRing &tr,
-                                           const LatticeDiv &ld, int64_t pix, const float4 *qtab, float &pe,
-                                           float &pb, float &pv, float &pw, int &nn, int &nm) {
+                                           const LatticeDiv &ld, int64_t pix, int mline, const float4 *qtab,
+                                           float &pe, float &pb, float &pv, float &pw, int &nn, int &nm) {
     const int q = R.nr >> 2;
     int Xi;
     float Xf;
     lattice_position(tr, ld, q, Xi, Xf);
-    const float fr = ((R.flags & RP_SHIFTED) ? 0.5f : 0.0f) - Xf;
+    const int sh = (R.flags & RP_SHIFTED) ? 1 : 0;
+    const float fr = (sh ? 0.5f : 0.0f) - Xf;
+    const int cm = mline * q - sh;
     int kl, kh;
     window(R, fr, kl, kh);
     int kk = Xi + kl;
@@ -118,10 +143,10 @@ __device__ __forceinline__ void band_pairs(const MapArgs &a, const RingPair &R, 
         float sinu, h;
         sin_hav<MODE>(u, sinu, h);
         const float s2 = fmaf(R.B, h, R.A);
-        const int p = R.start + kk;
+        const int p = R.start + (mline < 0 ? kk : mirror_index(R, cm, kk));
         kk = (kk + 1 == R.nr) ? 0 : kk + 1;
         if (s2 >= a.Tlo && s2 <= a.Thi && exact_member(a, pix, p))
-            pixel_pair<KIND, MODE>(a, R, qtab, u, p, pe, pb, pv, pw, nn, nm);
+            pixel_pair<KIND, MODE>(a, R, qtab, mline < 0 ? u : -u, p, pe, pb, pv, pw, nn, nm);
     }
 }
 
@@ -624,14 +649,27 @@ __device__ __forceinline__ bool toeplitz_tile_wanted(const MapArgs &a, int64_t t
     return a.toe_ring[tr0.i0 - 1] != 0;
 }
 
+// mirror line m of two targets on one ring (pix2 the image of pix about
+// the meridian m pi/4; tr is the ring position of pix): j + j2 + s = m q
+// (mod 4 q)
+__device__ __forceinline__ int mirror_line(const TargetRing &tr, int64_t pix, int64_t pix2) {
+    const int j2 = tr.j0 + (int)(pix2 - pix);
+    return ((tr.j0 + j2 + tr.s0) % tr.nr0) / tr.q0;
+}
+
 // guard-band pairs of the ring-pair entries in mask, then the summed
-// normalisation (Sect. 2.4) of the target from its raw sums
+// normalisation (Sect. 2.4) of target t from its raw sums.  tg is the target
+// whose window and geometry the sums were taken with: t itself, or the
+// partner of a mirror pair (general_target2) when t is the pair's image.
 template <int KIND>
-__device__ __forceinline__ void band_finish(const MapArgs &a, int64_t t, const float4 *qtab, unsigned long long mask,
-                                            double se, double sb, double sv, double sw, int NN, int NM) {
+__device__ __forceinline__ void band_finish(const MapArgs &a, int64_t t, int64_t tg, const float4 *qtab,
+                                            unsigned long long mask, double se, double sb, double sv, double sw,
+                                            int NN, int NM) {
     const int64_t pix = a.targets[t];
-    const TargetRing tr = target_ring(a.N0, pix);
+    const int64_t pixg = tg == t ? pix : a.targets[tg];
+    const TargetRing tr = target_ring(a.N0, pixg);
     const LatticeDiv ld = lattice_div(tr);
+    const int mline = tg == t ? -1 : mirror_line(tr, pixg, pix);
     const int64_t row0 = (int64_t)(tr.i0 - 1) * a.kmax;
     const int nent = a.counts[tr.i0 - 1];
     float pe = 0.f, pb = 0.f, pv = 0.f, pw = 0.f;
@@ -639,9 +677,9 @@ __device__ __forceinline__ void band_finish(const MapArgs &a, int64_t t, const f
         if (!((mask >> min(e, 63)) & 1ull)) continue;
         const RingPair R = a.table[row0 + e];
         const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
-        if (mode == 0) band_pairs<KIND, 0>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, NN, NM);
-        else if (mode == 1) band_pairs<KIND, 1>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, NN, NM);
-        else band_pairs<KIND, 2>(a, R, tr, ld, pix, qtab, pe, pb, pv, pw, NN, NM);
+        if (mode == 0) band_pairs<KIND, 0>(a, R, tr, ld, pix, mline, qtab, pe, pb, pv, pw, NN, NM);
+        else if (mode == 1) band_pairs<KIND, 1>(a, R, tr, ld, pix, mline, qtab, pe, pb, pv, pw, NN, NM);
+        else band_pairs<KIND, 2>(a, R, tr, ld, pix, mline, qtab, pe, pb, pv, pw, NN, NM);
     }
     const double SW = sw + (double)pw;
     float me = 0.f, mb = 0.f, vv = 0.f;
@@ -663,14 +701,44 @@ __device__ __forceinline__ void band_finish(const MapArgs &a, int64_t t, const f
 // call keeps the general loop's registers free of it); a points to a
 // __grid_constant__ kernel parameter or to global memory
 template <int KIND>
-__device__ __noinline__ void band_finish_call(const MapArgs *a, int64_t t, const float4 *qtab,
+__device__ __noinline__ void band_finish_call(const MapArgs *a, int64_t t, int64_t tg, const float4 *qtab,
                                               unsigned long long mask, double se, double sb, double sv, double sw,
                                               int NN, int NM) {
-    band_finish<KIND>(*a, t, qtab, mask, se, sb, sv, sw, NN, NM);
+    band_finish<KIND>(*a, t, tg, qtab, mask, se, sb, sv, sw, NN, NM);
+}
+
+// the end of a general target: normalised at once without guard-band
+// pairs; else its raw sums go to a slot (slot tag: the work-list position
+// times two, plus one for the image of a mirror pair), or, without a free
+// slot, band_finish runs in place
+template <int KIND>
+__device__ __forceinline__ void general_finish(const MapArgs &a, int64_t t, int64_t tg, int64_t tag,
+                                               const float4 *qtab, const GenBand &gb, unsigned long long mask,
+                                               float SE, float cSE, float SB, float cSB, float SV, float SW,
+                                               float cSW, int NN, int NM) {
+    if (!mask) {
+        finalise(a, t, SE, cSE, SB, cSB, SV, 0.f, SW, cSW, NN, NM);
+        return;
+    }
+    const double se = (double)SE - (double)cSE, sb = (double)SB - (double)cSB, sw = (double)SW - (double)cSW;
+    const unsigned long long slot = atomicAdd(gb.counts, 1ull);
+    if (slot < (unsigned long long)gb.cap_slots) {
+        double *raw = gb.raw + 4 * slot;
+        raw[0] = se;
+        raw[1] = sb;
+        raw[2] = (double)SV;
+        raw[3] = sw;
+        gb.cnt[2 * slot] = NN;
+        gb.cnt[2 * slot + 1] = NM;
+        gb.idx[slot] = tag;
+        gb.mask[slot] = mask;
+    } else {
+        band_finish_call<KIND>(&a, t, tg, qtab, mask, se, sb, (double)SV, sw, NN, NM);
+    }
 }
 
 // one target of a general output ring (one thread); gidx is its position in
-// the general list.  Guard-band pairs are left to band_finish.
+// the general work list.  Guard-band pairs are left to band_finish.
 template <int KIND>
 __device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, int64_t gidx, const float4 *qtab,
                                                const GenBand &gb) {
@@ -698,25 +766,234 @@ __device__ __forceinline__ void general_target(const MapArgs &a, int64_t t, int6
         NN += nn;
         NM += nm;
     }
-    if (!mask) {
-        finalise(a, t, SE, cSE, SB, cSB, SV, 0.f, SW, cSW, NN, NM);
-        return;
-    }
-    const double se = (double)SE - (double)cSE, sb = (double)SB - (double)cSB, sw = (double)SW - (double)cSW;
-    const unsigned long long slot = atomicAdd(gb.counts, 1ull);
-    if (slot < (unsigned long long)gb.cap_slots) {
-        double *raw = gb.raw + 4 * slot;
-        raw[0] = se;
-        raw[1] = sb;
-        raw[2] = (double)SV;
-        raw[3] = sw;
-        gb.cnt[2 * slot] = NN;
-        gb.cnt[2 * slot + 1] = NM;
-        gb.idx[slot] = gidx;
-        gb.mask[slot] = mask;
+    general_finish<KIND>(a, t, t, 2 * gidx, qtab, gb, mask, SE, cSE, SB, cSB, SV, SW, cSW, NN, NM);
+}
+
+// ------------------------------------------------------------------------
+// Mirror pairs of general targets.  Every HEALPix ring is symmetric about
+// the meridians phi = m pi/4 (m = 0..3): the pixel centred at azimuth phi
+// has an image at m pi/2 - phi on the same ring.  Two targets that are
+// images of each other see mirror-image neighbourhoods on every bin ring:
+// the pair (image target, image of bin pixel k) has the azimuth offset -u
+// of the pair (target, k), hence the same chord, filter weight and y, and
+// x -> -x (cos 2psi unchanged, sin 2psi negated).  general_target2 takes
+// both targets in one thread and evaluates each pair's geometry once for
+// the two; memberships outside the guard band follow from the shared s^2,
+// those inside it are decided in float64 for each target on its own pixels.
+// ------------------------------------------------------------------------
+struct PairSums {
+    float e, b, v, w;
+};
+
+// one member pair of the target and of its image: bin pixel data g (target)
+// and h (image) at lattice offset kf
+template <int KIND, int MODE>
+__device__ __forceinline__ void member_pair2(const MapArgs &a, const RingPair &R, const float4 *qtab, float u0,
+                                             float kf, const float4 &g, const float4 &h, PairSums &P,
+                                             PairSums &M) {
+    const float u = fmaf(kf, R.dphi, u0);
+    float sinu, hv;
+    sin_hav<MODE>(u, sinu, hv);
+    const float s2 = fmaf(R.B, hv, R.A);
+    const float x = R.mrho0 * sinu;
+    const float y = fmaf(R.D, hv, R.C);
+    const float xx = x * x;
+    const float cc = fmaf(y, y, -xx);
+    const float ss = -2.0f * x * y;
+    float Q, w;
+    if (KIND == SMART_FILTER_POLY) {
+        const float d2 = sep2_from_chord2(s2);
+        const float qn1 = a.f.qnorm * a.f.inv_ap2;
+        const float t = fmaf(d2, -qn1 * a.f.inv_ap2, qn1);
+        Q = d2 * t;
+        w = fmaf(Q, fmaf(d2, fmaf(d2, 2.0f / 189.0f, 1.0f / 15.0f), 1.0f / 3.0f), t);
     } else {
-        band_finish_call<KIND>(&a, t, qtab, mask, se, sb, (double)SV, sw, NN, NM);
+        Q = qtab_eval_member(qtab, s2, a.f.tab_scale);
+        w = __fdividef(Q, fmaf(y, y, xx) + 1e-30f);
     }
+    const float QQ = Q * Q;
+    P.e = fmaf(w, fmaf(g.x, cc, g.y * ss), P.e);
+    P.b = fmaf(w, fmaf(g.y, cc, -g.x * ss), P.b);
+    P.v = fmaf(QQ, g.z, P.v);
+    P.w += g.w;
+    M.e = fmaf(w, fmaf(h.x, cc, -h.y * ss), M.e);
+    M.b = fmaf(w, fmaf(h.y, cc, h.x * ss), M.b);
+    M.v = fmaf(QQ, h.z, M.v);
+    M.w += h.w;
+}
+
+// certain members of both targets: the target's bin pixels p1 .. p1 + cnt - 1
+// upwards, the image's p2 .. p2 - cnt + 1 downwards (cnt >= 1, neither run
+// crossing the ring's seam); loads one iteration ahead, last pair peeled
+template <int KIND, int MODE>
+__device__ __forceinline__ void certain_run2(const MapArgs &a, const RingPair &R, const float4 *qtab, float u0,
+                                             float kf, int p1, int p2, int cnt, PairSums &P, PairSums &M) {
+    const float4 *pp = a.PX + p1;
+    const float4 *qq = a.PX + p2;
+    float4 gn = __ldg(pp), hn = __ldg(qq);
+    const int last = cnt - 1;
+#pragma unroll 4
+    for (int i = 0; i < last; ++i) {
+        const float4 g = gn, h = hn;
+        gn = __ldg(pp + i + 1);
+        hn = __ldg(qq - i - 1);
+        member_pair2<KIND, MODE>(a, R, qtab, u0, kf, g, h, P, M);
+        kf += 1.0f;
+    }
+    member_pair2<KIND, MODE>(a, R, qtab, u0, kf, gn, hn, P, M);
+}
+
+// a tested member of both targets (bin pixels p1 and p2), as pixel_pair
+template <int KIND, int MODE>
+__device__ __forceinline__ void pixel_pair2(const MapArgs &a, const RingPair &R, const float4 *qtab, float u, int p1,
+                                            int p2, PairSums &P, PairSums &M, int &nn, int &nn2, int &nm) {
+    float sinu, hv;
+    sin_hav<MODE>(u, sinu, hv);
+    const float s2 = fmaf(R.B, hv, R.A);
+    const float x = R.mrho0 * sinu;
+    const float y = fmaf(R.D, hv, R.C);
+    const float xx = x * x;
+    const float sd2 = fmaf(y, y, xx);
+    const float cc = fmaf(y, y, -xx);
+    const float ss = -2.0f * x * y;
+    const float Q = filter_Q<KIND>(a.f, qtab, s2);
+    const float w = sd2 > 1e-30f ? __fdividef(Q, sd2) : 0.f;
+    const float QQ = Q * Q;
+    const float4 g = __ldg(a.PX + p1), h = __ldg(a.PX + p2);
+    P.e = fmaf(w, fmaf(g.x, cc, g.y * ss), P.e);
+    P.b = fmaf(w, fmaf(g.y, cc, -g.x * ss), P.b);
+    P.v = fmaf(QQ, g.z, P.v);
+    P.w += g.w;
+    M.e = fmaf(w, fmaf(h.x, cc, -h.y * ss), M.e);
+    M.b = fmaf(w, fmaf(h.y, cc, h.x * ss), M.b);
+    M.v = fmaf(QQ, h.z, M.v);
+    M.w += h.w;
+    nn += __ldg(a.NP + p1);
+    nn2 += __ldg(a.NP + p2);
+    nm += 1;
+}
+
+// general_segment for a target and its image about the meridian mline pi/4:
+// the window, the tested offsets and the run are the target's; the image
+// reads the mirror image of every bin pixel.  The run is cut where either
+// of the two crosses its ring's seam (at most three pieces: the window is
+// never longer than the ring).
+template <int KIND, int MODE>
+__device__ __forceinline__ void general_segment2(const MapArgs &a, const RingPair &R, const TargetRing &tr,
+                                                 const LatticeDiv &ld, int mline, const float4 *qtab, PairSums &P,
+                                                 PairSums &M, int &nn, int &nn2, int &nm, int &nband_out) {
+    const int q = R.nr >> 2;
+    int Xi;
+    float Xf;
+    lattice_position(tr, ld, q, Xi, Xf);
+    const int sh = (R.flags & RP_SHIFTED) ? 1 : 0;
+    const float fr = (sh ? 0.5f : 0.0f) - Xf;
+    const int cm = mline * q - sh;
+    int kl, kh;
+    window(R, fr, kl, kh);
+    int il = max(kl, (int)ceilf(-fr - R.hw_in)), ih = min(kh, (int)floorf(-fr + R.hw_in));
+    const float u0 = fr * R.dphi;
+    int nband = 0;
+    nband_out = 0;
+    if (kl > kh) return;      // no offset in the window
+    int ilc = il, ihc = ih;
+    if (il > ih) {            // no certain member: the run grows from the offset nearest the target
+        const int ks = min(max(__float2int_rn(-fr), kl), kh);
+        const float u = fmaf((float)ks, R.dphi, u0);
+        float sinu, hv;
+        sin_hav<MODE>(u, sinu, hv);
+        const float s2 = fmaf(R.B, hv, R.A);
+        ilc = ihc = ks;
+        if (s2 < a.Tlo) {
+            il = ih = ks;
+        } else {
+            nband += s2 <= a.Thi ? 1 : 0;
+            il = ks + 1;
+            ih = ks;
+        }
+    }
+    if (ilc > kl || ihc < kh)
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int k0 = side == 0 ? kl : ihc + 1, k1 = side == 0 ? ilc - 1 : kh;
+        for (int i = 0; i <= k1 - k0; ++i) {
+            const int k = side == 0 ? k1 - i : k0 + i;      // from the run outward
+            const float u = fmaf((float)k, R.dphi, u0);
+            float sinu, hv;
+            sin_hav<MODE>(u, sinu, hv);
+            const float s2 = fmaf(R.B, hv, R.A);
+            if (s2 < a.Tlo) {
+                if (side == 0 && k == il - 1) il = k;
+                else if (side == 1 && k == ih + 1) ih = k;
+                else {
+                    const int kk = wrap_start(R, Xi, k);
+                    pixel_pair2<KIND, MODE>(a, R, qtab, u, R.start + kk, R.start + mirror_index(R, cm, kk), P, M,
+                                            nn, nn2, nm);
+                }
+            } else {
+                nband += s2 <= a.Thi ? 1 : 0;
+            }
+        }
+    }
+    const int len = ih - il + 1;
+    if (len > 0) {
+        int kk = wrap_start(R, Xi, il), mm = mirror_index(R, cm, kk), left = len;
+        float kf = (float)il;
+#pragma unroll 1
+        for (int piece = 0; piece < 3 && left > 0; ++piece) {
+            const int cnt = min(left, min(R.nr - kk, mm + 1));
+            certain_run2<KIND, MODE>(a, R, qtab, u0, kf, R.start + kk, R.start + mm, cnt, P, M);
+            nn += __ldg(a.NPRE + R.start + kk + cnt) - __ldg(a.NPRE + R.start + kk);
+            nn2 += __ldg(a.NPRE + R.start + mm + 1) - __ldg(a.NPRE + R.start + mm + 1 - cnt);
+            left -= cnt;
+            kf += (float)cnt;
+            kk += cnt;
+            kk = kk == R.nr ? 0 : kk;
+            mm -= cnt;
+            mm = mm < 0 ? R.nr - 1 : mm;
+        }
+        nm += len;
+    }
+    nband_out = nband;
+}
+
+// a target t and its image t2 about a meridian m pi/4 (one thread); wpos is
+// their position in the general work list
+template <int KIND>
+__device__ __forceinline__ void general_target2(const MapArgs &a, int64_t t, int64_t t2, int64_t wpos,
+                                                const float4 *qtab, const GenBand &gb) {
+    const int64_t pix = a.targets[t];
+    const TargetRing tr = target_ring(a.N0, pix);
+    const LatticeDiv ld = lattice_div(tr);
+    const int mline = mirror_line(tr, pix, a.targets[t2]);
+    const int64_t row0 = (int64_t)(tr.i0 - 1) * a.kmax;
+    const int nent = a.counts[tr.i0 - 1];
+    float SE = 0.f, SB = 0.f, SV = 0.f, SW = 0.f, SE2 = 0.f, SB2 = 0.f, SV2 = 0.f, SW2 = 0.f;
+    int NN = 0, NN2 = 0, NM = 0;
+    unsigned long long mask = 0;
+    for (int e = 0; e < nent; ++e) {
+        const RingPair R = a.table[row0 + e];
+        const int mode = (R.flags & RP_WIDE) ? 2 : (((R.hw + 1.0f) * R.dphi <= 0.05f) ? 0 : 1);
+        PairSums P{0.f, 0.f, 0.f, 0.f}, M{0.f, 0.f, 0.f, 0.f};
+        int nn = 0, nn2 = 0, nm = 0, nb = 0;
+        if (mode == 0) general_segment2<KIND, 0>(a, R, tr, ld, mline, qtab, P, M, nn, nn2, nm, nb);
+        else if (mode == 1) general_segment2<KIND, 1>(a, R, tr, ld, mline, qtab, P, M, nn, nn2, nm, nb);
+        else general_segment2<KIND, 2>(a, R, tr, ld, mline, qtab, P, M, nn, nn2, nm, nb);
+        mask |= nb > 0 ? 1ull << min(e, 63) : 0ull;
+        SE += P.e;
+        SB += P.b;
+        SV += P.v;
+        SW += P.w;
+        SE2 += M.e;
+        SB2 += M.b;
+        SV2 += M.v;
+        SW2 += M.w;
+        NN += nn;
+        NN2 += nn2;
+        NM += nm;
+    }
+    general_finish<KIND>(a, t, t, 2 * wpos, qtab, gb, mask, SE, 0.f, SB, 0.f, SV, SW, 0.f, NN, NM);
+    general_finish<KIND>(a, t2, t, 2 * wpos + 1, qtab, gb, mask, SE2, 0.f, SB2, 0.f, SV2, SW2, 0.f, NN2, NM);
 }
 
 }  // namespace smart

@@ -110,7 +110,7 @@ extern "C" void smart_destroy(smart_ctx *c) {
                     c->own_np, c->keys, c->keys_alt, c->vals, c->vals_alt, c->offsets, c->rec_geo,
                     c->rec_shear, c->rec_radec, c->hist, c->hist_scan, c->scan_tmp, c->ring_lat, c->d_invalid,
                     c->tiles, c->tile_flag, c->qtab, c->np_prefix, c->d_work, c->toe_info, c->toe_geo,
-                    c->toe_ring, c->gen_list, c->gal_tiles, c->raw, c->band, c->d_band_count,
+                    c->toe_ring, c->gen_list, c->gen_work, c->gal_tiles, c->raw, c->band, c->d_band_count,
                     c->d_status, c->d_fp64_count, c->bary_off, c->bary_geo, c->bary_sh, c->bary_keys,
                     c->bary_cnt, c->bary_vec, c->bary_wr, c->raw_m, c->avg_buf, c->gen_band, c->d_gen_count,
                     c->proj_plane, c->proj_xy, c->proj_sh, c->proj_txy, c->qtab_plane, c->annulus_buf};
@@ -389,6 +389,21 @@ extern "C" smart_status smart_set_band_slot_limit(smart_ctx *c, int64_t n_slots)
     if (!c) return SMART_E_ARG;
     if (n_slots < 0) return fail(c, SMART_E_ARG, "smart_set_band_slot_limit: negative limit");
     c->band_slot_limit = n_slots;
+    return SMART_OK;
+}
+
+extern "C" smart_status smart_get_general_pairs(smart_ctx *c, int32_t *pairs, int64_t cap, int64_t *n_pairs,
+                                                int64_t *n_single) {
+    if (!c || !n_pairs || !n_single) return SMART_E_ARG;
+    if (c->gen_version != c->targets_version)
+        return fail(c, SMART_E_STATE, "smart_get_general_pairs: no pixel map since the targets were set");
+    *n_pairs = c->n_work_pairs;
+    *n_single = c->n_work - c->n_work_pairs;
+    if (pairs && c->n_work_pairs > 0) {
+        if (cap < c->n_work_pairs) return fail(c, SMART_E_ARG, "smart_get_general_pairs: output too small");
+        return check_cuda(c, cudaMemcpyAsync(pairs, c->gen_work, (size_t)c->n_work_pairs * sizeof(int2),
+                                             cudaMemcpyDeviceToDevice, c->stream), "smart_get_general_pairs");
+    }
     return SMART_OK;
 }
 

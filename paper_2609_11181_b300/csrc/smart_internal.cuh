@@ -350,6 +350,8 @@ struct smart_ctx {
     unsigned char *toe_ring = nullptr;               // per output ring: all ring pairs Toeplitz
     int32_t *gen_list = nullptr;                     // targets handled by the general kernel
     int64_t cap_gen_list = 0, n_gen = 0;
+    int2 *gen_work = nullptr;                        // its work: mirror pairs (target, image), then singles (target, -1)
+    int64_t cap_gen_work = 0, n_work = 0, n_work_pairs = 0;
     int64_t targets_version = 0, gen_version = -1;
     int64_t *gal_tiles = nullptr;                    // brute force: groups of up to 4 targets
     int64_t cap_gal_tiles = 0, n_gal_tiles = 0, gal_tiles_version = -1;

@@ -158,6 +158,56 @@ def test_maps_bin_and_aperture_extremes(cuda_device, no, nb, th, filt, rad):
     ctx.close()
 
 
+def test_general_mirror_pairs(cuda_device):
+    """General targets whose mirror image about a meridian m pi/4 is a target
+    too run in pairs that share each pair's geometry.  The cap is centred on
+    the meridian pi/4 at polar ring 20 of NSIDE 64 with the aperture of the
+    in-place test below (every target of ring 20 has guard-band pairs), so
+    nearly every general target is paired and the images' guard-band pairs
+    are decided from the shared window.  Checked: the pairs are mirror images
+    (one ring, azimuths summing to a multiple of pi/2) and disjoint; the map
+    against the oracle; one slot (images finished in place) bit-identical."""
+    nside, ring = 64, 20
+    z = 1.0 - ring * ring / (3.0 * nside * nside)
+    rho = math.sqrt((1.0 - z) * (1.0 + z))
+    theta_arcmin = 2.0 * math.asin(rho * math.sin(3 * (2 * math.pi / (4 * ring)) / 2)) / ARCMIN
+    dec_ring = math.degrees(math.asin(z))
+    cat = catalog(24, 60_000, 45.0, dec_ring, 8.0, w_range=(0.5, 1.5))
+    tg = cap_targets(nside, 45.0, dec_ring, 5.0)
+    dev = cuda_device
+    ctx = api.Context(nside, theta_arcmin, "schirmer", nside_bin=nside)
+    c = cat.to(dev)
+    ctx.set_targets(torch.from_numpy(tg).to(dev))
+    ctx.bin_galaxies(c.ra_deg, c.dec_deg, c.e1, c.e2, c.w)
+    a = ctx.map_pixel()
+    ctx.sync(60)
+    pairs, n_single = ctx.general_pairs()
+    gen = ctx.general_targets().cpu().numpy()
+    p = pairs.cpu().numpy()
+    assert 2 * len(p) + n_single == len(gen)
+    assert len(p) >= 0.4 * len(gen)
+    flat = p.ravel()
+    assert np.unique(flat).size == flat.size and np.isin(flat, gen).all()
+    v = oracle.pix2vec(nside, tg[flat]).reshape(-1, 2, 3)
+    assert np.array_equal(v[:, 0, 2], v[:, 1, 2])
+    phi = np.arctan2(v[..., 1], v[..., 0])
+    q = (phi[:, 0] + phi[:, 1]) / (math.pi / 2)
+    assert np.abs(q - np.round(q)).max() < 1e-9
+    on_ring = [i for i in flat if oracle.pix_info(nside, int(tg[i]))[0] == ring]
+    assert len(on_ring) >= 8
+    _, rpx = _oracle_maps(cat, tg, nside, nside, theta_arcmin, 2)
+    _check(a, rpx, "mirror pairs")
+    n_fp64 = ctx.fp64_decisions()
+    assert n_fp64 >= 2 * len(on_ring)
+    ctx.set_band_slot_limit(1)
+    b = ctx.map_pixel()
+    ctx.sync(60)
+    assert ctx.fp64_decisions() == n_fp64
+    for k in ("map_e", "map_b", "var", "sum_w", "count", "members"):
+        assert torch.equal(a[k], b[k]), k
+    ctx.close()
+
+
 def test_pixel_mode_binned_field(cuda_device):
     """Pixel-based workload shape (Poisson counts, SIS field) at nside 512, Schirmer 10'."""
     nside = 512

@@ -67,6 +67,8 @@ def test_stateless_calls_reject_bad_arguments():
     assert lib.smart_pix2vec(64, None, 3, None, None) == 1
     assert lib.smart_sync(None, 1.0) == 1
     assert lib.smart_set_band_slot_limit(None, 1) == 1
+    n1, n2 = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.smart_get_general_pairs(None, None, 0, ctypes.byref(n1), ctypes.byref(n2)) == 1
     assert lib.smart_last_error(None) == b"null context"
     lib.smart_destroy(None)
     fl = ctypes.c_double(0.0)
