@@ -428,11 +428,24 @@ __device__ __forceinline__ void toe_stage(const MapArgs &a, const ToeStage *par,
     const ToeStage t = tile_param(a, par, row0, e, jbase);
     if (t.L > 0) {
         const int nseg = min(toe_segn<NC>(), nslots + t.L + 7);
-        // -nr < k0 + m < 2 nr for every staged m (the window is shorter than the ring)
-        for (int m = tid; m < nseg; m += NT) {
-            int kk = t.k0 + m;
-            kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
-            cp_async16(&seg[b][tpos(m)], a.PX + t.start + kk);
+        if (t.k0 >= 0 && t.k0 + nseg <= t.nr) {
+            // no seam: pixel m = tid + NT i sits in row (tid >> 3) + 4 i and
+            // column tid & 7, so tpos(m) is one of two per-thread positions
+            // (even or odd i) plus NT i: copies with immediate offsets
+            const float4 *g = a.PX + t.start + t.k0 + tid;
+            const int r0 = tid >> 3, c = tid & 7;
+            float4 *se = &seg[b][(r0 << 3) | (c ^ r0)];
+            float4 *so = &seg[b][(r0 << 3) | (c ^ (r0 + 4))];
+#pragma unroll
+            for (int i = 0; i < (toe_segn<NC>() + NT - 1) / NT; ++i)
+                if (tid + NT * i < nseg) cp_async16(((i & 1) ? so : se) + NT * i, g + NT * i);
+        } else {
+            // -nr < k0 + m < 2 nr for every staged m (the window is shorter than the ring)
+            for (int m = tid; m < nseg; m += NT) {
+                int kk = t.k0 + m;
+                kk += kk < 0 ? t.nr : (kk >= t.nr ? -t.nr : 0);
+                cp_async16(&seg[b][tpos(m)], a.PX + t.start + kk);
+            }
         }
         for (int c = tid; c < t.L; c += NT) cp_async16(&geo[b][c], a.toe_geo + t.off + t.da + c);
     }
@@ -503,12 +516,13 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
 #pragma unroll
     for (int r = 0; r < RB; ++r) any |= (s0 + r < nslots) && slot_t[s0 + r] >= 0;
     float SE[RB], SB[RB], SV[RB], SW[RB];
-    int NN[RB], NM[RB];
+    int NNc[RB];       // galaxies in the windows of slot tid + NT r (coalesced count loads)
+    int NMs = 0;       // member pixels outside the guard band: the same for every slot
     float pe[RB], pb[RB], pv[RB], pw[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         SE[r] = SB[r] = SV[r] = SW[r] = 0.f;
-        NN[r] = NM[r] = 0;
+        NNc[r] = 0;
         pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
     }
 
@@ -554,34 +568,6 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                     }
                 }
             }
-            // galaxies of the slots' windows [k0 + s, k0 + s + L) from the
-            // count prefix in global memory: after the pairs (the window never
-            // passes the ring's end more than once; tiles at the seam take the
-            // wrapped indices)
-            const int lo0 = cur.k0 + s0;
-            const bool seam = lo0 < 0 || lo0 + RB - 1 + L >= cur.nr;
-            int pa[RB], pz[RB];
-            if (!seam) {
-                const int32_t *pp = a.NPRE + cur.start + lo0;
-#pragma unroll
-                for (int r = 0; r < RB; ++r) {
-                    pa[r] = __ldg(pp + r);
-                    pz[r] = __ldg(pp + r + L);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < RB; ++r) {
-                    const int lo = lo0 + r, hi = lo + L;
-                    const int klo = lo - wraps(lo, cur.nr) * cur.nr, khi = hi - wraps(hi, cur.nr) * cur.nr;
-                    pa[r] = __ldg(a.NPRE + cur.start + klo);
-                    pz[r] = __ldg(a.NPRE + cur.start + khi) + (wraps(hi, cur.nr) - wraps(lo, cur.nr)) * cur.tot;
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                NN[r] += pz[r] - pa[r];
-                NM[r] += L;
-            }
             if ((e & 1) || e + 1 == nent) {
 #pragma unroll
                 for (int r = 0; r < RB; ++r) {
@@ -602,7 +588,44 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                 pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
             }
         }
+        // galaxies of the windows [k0 + s, k0 + s + L) from the count prefix
+        // in global memory, after the pairs: lane tid takes the slots tid +
+        // NT r, so each load instruction reads consecutive words (read before
+        // the pairs, or for all ring pairs at the start of the tile, they
+        // were slower).  The window never passes the ring's end more than
+        // once; tiles at the seam take the wrapped indices.
+        if (L > 0) {
+            const int k0 = cur.k0;
+            if (k0 >= 0 && k0 + nslots - 1 + L < cur.nr) {
+                const int32_t *pp = a.NPRE + cur.start + k0 + tid;
+#pragma unroll
+                for (int r = 0; r < RB; ++r)
+                    if (tid + NT * r < nslots) NNc[r] += __ldg(pp + NT * r + L) - __ldg(pp + NT * r);
+            } else {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int lo = k0 + tid + NT * r, hi = lo + L;
+                    if (tid + NT * r >= nslots) continue;
+                    const int klo = lo - wraps(lo, cur.nr) * cur.nr, khi = hi - wraps(hi, cur.nr) * cur.nr;
+                    NNc[r] += __ldg(a.NPRE + cur.start + khi) + (wraps(hi, cur.nr) - wraps(lo, cur.nr)) * cur.tot -
+                              __ldg(a.NPRE + cur.start + klo);
+                }
+            }
+            NMs += L;
+        }
     }
+    // the counts to slot order through shared memory: the segment buffer
+    // nent & 1 was last read before the final ring pair's barrier and has no
+    // copy in flight (two words per slot fit in it many times over)
+    int *cnt_s = reinterpret_cast<int *>(&seg[nent & 1][0]);
+    int *nm_s = cnt_s + TS;
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        cnt_s[tid + NT * r] = NNc[r];
+        nm_s[tid + NT * r] = NMs;
+    }
+    __syncwarp();
     // ---- guard-band offsets, after every ring pair (the hot loop's
     // registers are dead here): decided per target in float64
     if (any) {
@@ -626,8 +649,8 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                     SB[r] += fmaf(G.x, px.y, G.z * px.x);
                     SV[r] += G.w * px.z;
                     SW[r] += px.w;
-                    NN[r] += __ldg(a.NP + p);
-                    NM[r] += 1;
+                    cnt_s[s0 + r] += __ldg(a.NP + p);
+                    nm_s[s0 + r] += 1;
                 }
             }
         }
@@ -636,7 +659,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         const int ti = (s0 + r < nslots) ? slot_t[s0 + r] : -1;
-        if (ti >= 0) finalise(a, tb + ti, SE[r], 0.f, SB[r], 0.f, SV[r], 0.f, SW[r], 0.f, NN[r], NM[r]);
+        if (ti >= 0) finalise(a, tb + ti, SE[r], 0.f, SB[r], 0.f, SV[r], 0.f, SW[r], 0.f, cnt_s[s0 + r], nm_s[s0 + r]);
     }
     __syncthreads();   // slot map and buffers are rewritten by the next tile
 }
