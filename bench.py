@@ -70,10 +70,11 @@ GENERAL_EXEC_FLOPS_PER_PAIR = {"schirmer": 49, "jarvis": 49, "poly": 53}
 # for both; the image's pairs have the target's geometry with x -> -x): the
 # geometry, filter and weight of a pair (36 flop with a table, 40 with the
 # polynomial filter, as counted above) serve two pairs, each of which adds
-# its E / B, variance and weight sums (14) and shares Q^2: 31 measured with a
-# tabulated filter (ncu, as above, NSIDE 2048 case; 30.7), 33 polynomial
-# (the count's difference of 4 per two pairs added).
-GENERAL_PAIRED_EXEC_FLOPS_PER_PAIR = {"schirmer": 31, "jarvis": 31, "poly": 33}
+# its E / B, variance and weight sums and shares Q^2 and the weighted
+# rotation terms Q cos 2psi, Q sin 2psi: 30 measured with a tabulated filter
+# (ncu, as above, NSIDE 2048 case), 32 polynomial (the count's difference of
+# 4 per two pairs added).
+GENERAL_PAIRED_EXEC_FLOPS_PER_PAIR = {"schirmer": 30, "jarvis": 30, "poly": 32}
 
 
 def _env_int(k, d):

@@ -516,13 +516,12 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
 #pragma unroll
     for (int r = 0; r < RB; ++r) any |= (s0 + r < nslots) && slot_t[s0 + r] >= 0;
     float SE[RB], SB[RB], SV[RB], SW[RB];
-    int NNc[RB];       // galaxies in the windows of slot tid + NT r (coalesced count loads)
-    int NMs = 0;       // member pixels outside the guard band: the same for every slot
+    int NN[RB], NM[RB];
     float pe[RB], pb[RB], pv[RB], pw[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         SE[r] = SB[r] = SV[r] = SW[r] = 0.f;
-        NNc[r] = 0;
+        NN[r] = NM[r] = 0;
         pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
     }
 
@@ -568,6 +567,35 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                     }
                 }
             }
+            // galaxies of the slots' windows [k0 + s, k0 + s + L) from the
+            // count prefix in global memory: after the pairs (the window never
+            // passes the ring's end more than once; tiles at the seam take the
+            // wrapped indices).  Read with lane t taking slots t + 32 r
+            // (coalesced) they were slower.
+            const int lo0 = cur.k0 + s0;
+            const bool seam = lo0 < 0 || lo0 + RB - 1 + L >= cur.nr;
+            int pa[RB], pz[RB];
+            if (!seam) {
+                const int32_t *pp = a.NPRE + cur.start + lo0;
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    pa[r] = __ldg(pp + r);
+                    pz[r] = __ldg(pp + r + L);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int lo = lo0 + r, hi = lo + L;
+                    const int klo = lo - wraps(lo, cur.nr) * cur.nr, khi = hi - wraps(hi, cur.nr) * cur.nr;
+                    pa[r] = __ldg(a.NPRE + cur.start + klo);
+                    pz[r] = __ldg(a.NPRE + cur.start + khi) + (wraps(hi, cur.nr) - wraps(lo, cur.nr)) * cur.tot;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                NN[r] += pz[r] - pa[r];
+                NM[r] += L;
+            }
             if ((e & 1) || e + 1 == nent) {
 #pragma unroll
                 for (int r = 0; r < RB; ++r) {
@@ -588,44 +616,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                 pe[r] = pb[r] = pv[r] = pw[r] = 0.f;
             }
         }
-        // galaxies of the windows [k0 + s, k0 + s + L) from the count prefix
-        // in global memory, after the pairs: lane tid takes the slots tid +
-        // NT r, so each load instruction reads consecutive words (read before
-        // the pairs, or for all ring pairs at the start of the tile, they
-        // were slower).  The window never passes the ring's end more than
-        // once; tiles at the seam take the wrapped indices.
-        if (L > 0) {
-            const int k0 = cur.k0;
-            if (k0 >= 0 && k0 + nslots - 1 + L < cur.nr) {
-                const int32_t *pp = a.NPRE + cur.start + k0 + tid;
-#pragma unroll
-                for (int r = 0; r < RB; ++r)
-                    if (tid + NT * r < nslots) NNc[r] += __ldg(pp + NT * r + L) - __ldg(pp + NT * r);
-            } else {
-#pragma unroll
-                for (int r = 0; r < RB; ++r) {
-                    const int lo = k0 + tid + NT * r, hi = lo + L;
-                    if (tid + NT * r >= nslots) continue;
-                    const int klo = lo - wraps(lo, cur.nr) * cur.nr, khi = hi - wraps(hi, cur.nr) * cur.nr;
-                    NNc[r] += __ldg(a.NPRE + cur.start + khi) + (wraps(hi, cur.nr) - wraps(lo, cur.nr)) * cur.tot -
-                              __ldg(a.NPRE + cur.start + klo);
-                }
-            }
-            NMs += L;
-        }
     }
-    // the counts to slot order through shared memory: the segment buffer
-    // nent & 1 was last read before the final ring pair's barrier and has no
-    // copy in flight (two words per slot fit in it many times over)
-    int *cnt_s = reinterpret_cast<int *>(&seg[nent & 1][0]);
-    int *nm_s = cnt_s + TS;
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < RB; ++r) {
-        cnt_s[tid + NT * r] = NNc[r];
-        nm_s[tid + NT * r] = NMs;
-    }
-    __syncwarp();
     // ---- guard-band offsets, after every ring pair (the hot loop's
     // registers are dead here): decided per target in float64
     if (any) {
@@ -649,8 +640,8 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
                     SB[r] += fmaf(G.x, px.y, G.z * px.x);
                     SV[r] += G.w * px.z;
                     SW[r] += px.w;
-                    cnt_s[s0 + r] += __ldg(a.NP + p);
-                    nm_s[s0 + r] += 1;
+                    NN[r] += __ldg(a.NP + p);
+                    NM[r] += 1;
                 }
             }
         }
@@ -659,7 +650,7 @@ __device__ __forceinline__ void toeplitz_tile(const MapArgs &a, int64_t tile, To
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
         const int ti = (s0 + r < nslots) ? slot_t[s0 + r] : -1;
-        if (ti >= 0) finalise(a, tb + ti, SE[r], 0.f, SB[r], 0.f, SV[r], 0.f, SW[r], 0.f, cnt_s[s0 + r], nm_s[s0 + r]);
+        if (ti >= 0) finalise(a, tb + ti, SE[r], 0.f, SB[r], 0.f, SV[r], 0.f, SW[r], 0.f, NN[r], NM[r]);
     }
     __syncthreads();   // slot map and buffers are rewritten by the next tile
 }
@@ -834,13 +825,16 @@ __device__ __forceinline__ void member_pair2(const MapArgs &a, const RingPair &R
         Q = qtab_eval_member(qtab, s2, a.f.tab_scale);
         w = __fdividef(Q, fmaf(y, y, xx) + 1e-30f);
     }
-    const float QQ = Q * Q;
-    P.e = fmaf(w, fmaf(g.x, cc, g.y * ss), P.e);
-    P.b = fmaf(w, fmaf(g.y, cc, -g.x * ss), P.b);
+    // the weighted rotation once for both targets: wc = Q cos 2psi and
+    // ws = Q sin 2psi (w = Q / sin^2 d; cc and ss carry sin^2 d), then two
+    // FMAs per sum
+    const float QQ = Q * Q, wc = w * cc, ws = w * ss;
+    P.e = fmaf(g.y, ws, fmaf(g.x, wc, P.e));
+    P.b = fmaf(-g.x, ws, fmaf(g.y, wc, P.b));
     P.v = fmaf(QQ, g.z, P.v);
     P.w += g.w;
-    M.e = fmaf(w, fmaf(h.x, cc, -h.y * ss), M.e);
-    M.b = fmaf(w, fmaf(h.y, cc, h.x * ss), M.b);
+    M.e = fmaf(-h.y, ws, fmaf(h.x, wc, M.e));
+    M.b = fmaf(h.x, ws, fmaf(h.y, wc, M.b));
     M.v = fmaf(QQ, h.z, M.v);
     M.w += h.w;
 }
