@@ -100,7 +100,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         self.f = open(self.path, "w")
         self.proc = subprocess.Popen([exe, f"--id={gpu_index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                      "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                      "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
 
     def stop(self):
         if self.proc is None:
@@ -986,7 +986,7 @@ def run_reference(args, world, rank):
     times, vals = [], []
     cb = None
     for k in range(args.warmup + args.steps):
-        cb, pairs, dt, m = cpu_baseline_pixel(wl, host_G, budget_s=max(2.0, 60.0 / (args.steps + args.warmup)), seed=k)
+        cb, pairs, dt, m = cpu_baseline_pixel(wl, host_G, budget_s=max(1.0, 60.0 / (args.steps + args.warmup)), seed=k)
         if k >= args.warmup:
             times.append(dt)
             vals.append(pairs / dt / 1e9)
@@ -1054,7 +1054,7 @@ def run_forms(args, world, rank, headline: dict) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="pixel4096",
