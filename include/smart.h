@@ -391,8 +391,9 @@ smart_status smart_timing_read(smart_ctx *ctx, int kernel, int64_t *launches, do
  * Positions (into the target array) of the targets that the last pixel map
  * sent to the general kernel; the others went to the Toeplitz kernel.
  * *n_gen (host) receives their number; idx (device, int32, capacity cap)
- * receives the positions unless NULL.  SMART_E_STATE before the first pixel
- * map after smart_set_targets.  Asynchronous on the context stream.
+ * receives the positions unless NULL.  The lists are built by
+ * smart_set_targets; SMART_E_STATE for an empty target set or after a
+ * smart_set_targets that failed.  Asynchronous on the context stream.
  */
 smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap, int64_t *n_gen);
 
@@ -406,7 +407,8 @@ smart_status smart_get_general_targets(smart_ctx *ctx, int32_t *idx, int64_t cap
  * *n_single (host) receive the number of pairs and of general targets left
  * unpaired (n_gen = 2 n_pairs + n_single); pairs (device, int32, capacity
  * cap pairs) receives the pairs' target positions as (lower, image) unless
- * NULL.  SMART_E_STATE before the first pixel map after smart_set_targets.
+ * NULL.  Built by smart_set_targets; SMART_E_STATE for an empty target set
+ * or after a smart_set_targets that failed.
  * Asynchronous on the context stream.
  */
 smart_status smart_get_general_pairs(smart_ctx *ctx, int32_t *pairs, int64_t cap, int64_t *n_pairs,

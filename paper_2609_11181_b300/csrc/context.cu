@@ -396,7 +396,7 @@ extern "C" smart_status smart_get_general_pairs(smart_ctx *c, int32_t *pairs, in
                                                 int64_t *n_single) {
     if (!c || !n_pairs || !n_single) return SMART_E_ARG;
     if (c->gen_version != c->targets_version)
-        return fail(c, SMART_E_STATE, "smart_get_general_pairs: no pixel map since the targets were set");
+        return fail(c, SMART_E_STATE, "smart_get_general_pairs: no tables for the current targets");
     *n_pairs = c->n_work_pairs;
     *n_single = c->n_work - c->n_work_pairs;
     if (pairs && c->n_work_pairs > 0) {
@@ -410,7 +410,7 @@ extern "C" smart_status smart_get_general_pairs(smart_ctx *c, int32_t *pairs, in
 extern "C" smart_status smart_get_general_targets(smart_ctx *c, int32_t *idx, int64_t cap, int64_t *n_gen) {
     if (!c || !n_gen) return SMART_E_ARG;
     if (c->gen_version != c->targets_version)
-        return fail(c, SMART_E_STATE, "smart_get_general_targets: no pixel map since the targets were set");
+        return fail(c, SMART_E_STATE, "smart_get_general_targets: no tables for the current targets");
     *n_gen = c->n_gen;
     if (idx && c->n_gen > 0) {
         if (cap < c->n_gen) return fail(c, SMART_E_ARG, "smart_get_general_targets: output too small");
